@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Benchmark of the 3DHEB bundling iteration on GB300.
+
+A step is one full iteration of the loop (resample, histogram, box passes,
+layer mix, advection with the halving step, Laplacian smoothing) over one
+synthetic graph resident in HBM. The default workload is the criteria-driven
+configuration the headline metric is quoted on: 5M edges between nodes of a
+perturbed 2048 x 2048 lattice, 8 k-means groups on (origin, destination),
+an 8 x 1024 x 1024 int64 histogram stack, r = 12, 4 passes, <= 64 samples per
+edge (delta = 2 px). Metric: sample-point updates per second (points advected
+per iteration x iterations / time).
+
+Prints one JSON line. `--impl reference` times the FP64 CPU oracle instead
+(bounded sample of the same workload, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sample_point_updates_per_s"
+UNIT = "updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lattice", choices=["lattice", "clustered", "small"])
+    ap.add_argument("--edges", type=int, default=0, help="override the edge count (testing)")
+    ap.add_argument("--rho", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, edges, seed_offset=0):
+    from paper_1504_02687_gb300 import synth
+
+    if name == "lattice":
+        kw = dict(seed=synth.SEED_BASE + 3 + seed_offset)
+        if edges:
+            kw["n_edges"] = edges
+        return synth.lattice_pattern(**kw)
+    if name == "clustered":
+        kw = dict(seed=synth.SEED_BASE + 2 + seed_offset)
+        if edges:
+            kw["n_edges"] = edges
+        return synth.clustered(**kw)
+    return synth.small(seed=synth.SEED_BASE + 1 + seed_offset)
+
+
+def describe(w, rho):
+    W, H = w.grid
+    return {
+        "workload": (f"{w.name}: {w.n_edges} edges, {w.n_groups} groups, {w.n_groups}x{H}x{W} "
+                     f"histogram stack, r={w.radius}, k={w.passes}, "
+                     + (f"{w.n_fixed} samples/edge" if w.n_fixed else
+                        f"<= {w.n_max} samples/edge (delta={w.delta} px)")),
+        "edges": w.n_edges, "groups": w.n_groups, "grid": [W, H], "radius": w.radius,
+        "passes": w.passes, "n_max": w.n_max, "n_fixed": w.n_fixed, "rho_dtype": rho,
+        "l2": "inputs larger than L2 (point buffers of the iteration exceed 129 MB)",
+    }
+
+
+def params_of(w, rho):
+    import paper_1504_02687_gb300 as pkg
+
+    return pkg.default_params(grid_w=w.grid[0], grid_h=w.grid[1], radius=w.radius,
+                              passes=w.passes, n_fixed=w.n_fixed, n_max=w.n_max,
+                              delta_px=w.delta,
+                              rho_dtype={"f32": 0, "bf16": 1, "f16": 2}[rho])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons, busy = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz, smax, pw = float(f[1]), float(f[2]), float(f[3])
+            except ValueError:
+                continue
+            sm.append(mhz)
+            busy.append((pw, mhz))
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": sorted(reasons)}
+        # under load: the samples at or above the median power draw
+        pw_med = statistics.median(p for p, _ in busy)
+        loaded = [m for p, m in busy if p >= pw_med] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho):
+    """Bytes one launch of each kernel must move (its roofline numerator).
+
+    advect+resample: read and write every point (8 B each way), per-edge count in and out,
+    group and weight (16 B), one read of the density stack, the histogram written once.
+    """
+    if kind == "advect_resample":
+        return 16 * N + 16 * E + GC * b_rho + 4 * GC
+    if kind == "resample":
+        return 16 * N + 16 * E + 4 * GC
+    if kind == "advect":
+        return 16 * N + 12 * E + GC * b_rho
+    if kind == "rowbox":
+        return GC * (4 + b_sum)
+    if kind == "colbox":
+        return 2 * GC * b_sum
+    if kind == "combine":
+        return GC * (b_sum + b_rho)
+    return 0
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_points.cu", "k_grid.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1504_02687_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind, workload_name):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    ent = d.get(workload_name, {}).get(kind)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(w, sample_edges):
+    """The FP64 oracle as it stands, single-threaded, one iteration on the first
+    `sample_edges` edges of the same graph (same grid, groups, filter)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    E = min(sample_edges, w.n_edges)
+    W_, H_, mp, sp, dp = oracle.grid_map(w.src_xy[:E], w.dst_xy[:E], w.grid[0], w.grid[1],
+                                         margin=w.radius)
+    off, xy = oracle.straight_polylines(sp, dp)
+    prm = oracle.Params(radius=w.radius, passes=w.passes, n_fixed=w.n_fixed, n_max=w.n_max,
+                        delta=w.delta)
+    t0 = time.perf_counter()
+    res = oracle.run(off, xy, w.group[:E], None if w.weight is None else w.weight[:E],
+                     w.n_groups, H_, W_, prm, 0, 1)
+    dt = time.perf_counter() - t0
+    n = int(res.off[-1])
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"1 iteration of the FP64 oracle on the first {E} of {w.n_edges} edges "
+                       f"({n} sample points, full {w.n_groups}x{H_}x{W_} grid), {dt:.1f} s")}
+
+
+def run_reference(args):
+    """The oracle arm: each step is one oracle iteration on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.edges)
+    oracle.build()
+    E = min(w.n_edges, 1_000_000)
+    W_, H_, mp, sp, dp = oracle.grid_map(w.src_xy[:E], w.dst_xy[:E], w.grid[0], w.grid[1],
+                                         margin=w.radius)
+    off, xy = oracle.straight_polylines(sp, dp)
+    prm = oracle.Params(radius=w.radius, passes=w.passes, n_fixed=w.n_fixed, n_max=w.n_max,
+                        delta=w.delta)
+    g = w.group[:E]
+    wt = None if w.weight is None else w.weight[:E]
+    it = 0
+    for _ in range(args.warmup):
+        r = oracle.run(off, xy, g, wt, w.n_groups, H_, W_, prm, it, 1)
+        off, xy, it = r.off, r.xy, it + 1
+    pts = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pts += int(off[-1]) if prm.n_fixed else 0
+        r = oracle.run(off, xy, g, wt, w.n_groups, H_, W_, prm, it, 1, keep_last=True)
+        if not prm.n_fixed:
+            pts += int(r.res_off[-1])
+        off, xy, it = r.off, r.xy, it + 1
+    dt = time.perf_counter() - t0
+    value = pts / dt
+    cfg = describe(w, "f64")
+    sample = (f"{args.steps} oracle iterations on the first {E} of {w.n_edges} edges of the "
+              f"workload, single-threaded FP64")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1504_02687_gb300 as pkg
+    from paper_1504_02687_gb300 import build as lib_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+    if rank == 0:
+        lib_build.build()
+    if dist:
+        dist.barrier()
+    lib_build.build()
+    # every rank bundles its own graph of the same configuration (independent problems)
+    w = make_workload(args.workload, args.edges, seed_offset=rank * 1000)
+    stream = torch.cuda.current_stream()
+    p = params_of(w, args.rho)
+    ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight, stream=stream)
+    info = pkg.bundle_get_info(ctx)
+    GC = info.n_groups * info.grid_w * info.grid_h
+    b_sum = info.sum_bits // 8
+    b_rho = 4 if args.rho == "f32" else 2
+
+    clocks = ClockSampler(dev_index)
+    pkg.bundle_iterate(ctx, max(args.warmup, 3) if args.warmup >= 3 else args.warmup)
+    pkg.bundle_sync(ctx)
+    done0 = pkg.bundle_get_info(ctx).points_processed
+    pkg.bundle_profile_enable(ctx, True)
+    pkg.bundle_profile_read(ctx)  # clears
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    pkg.bundle_iterate(ctx, args.steps)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    clk = clocks.stop()
+    prof = pkg.bundle_profile_read(ctx)
+    pkg.bundle_profile_enable(ctx, False)
+    info = pkg.bundle_get_info(ctx)
+    updates = info.points_processed - done0
+    E = info.n_edges
+    N_avg = updates / max(args.steps, 1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        u = torch.tensor([float(updates)], device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_updates = float(u.item())
+    else:
+        total_updates = float(updates)
+    value = total_updates / (ms / 1e3)
+
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    launches = sum(n for k, (t, n) in kern.items() if k != "hist_clear")
+    dom = max((k for k in kern if k != "hist_clear"), key=lambda k: kern[k][0])
+    dom_ms = kern[dom][0] / kern[dom][1]
+    dom_bytes = algorithmic_bytes(dom, N_avg, E, GC, b_sum, b_rho)
+    peak, peak_src = peaks()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = measured_traffic(dom, w.name)
+    per_kernel = {}
+    for k, (tms, n) in kern.items():
+        b = algorithmic_bytes(k, N_avg, E, GC, b_sum, b_rho)
+        per_kernel[k] = {"launches": n, "ms_per_launch": tms / n, "share": tms / max(ms, 1e-9),
+                         "algorithmic_gbs": (b / (tms / n / 1e3) / 1e9) if b else None}
+    step_bytes = (algorithmic_bytes("advect_resample", N_avg, E, GC, b_sum, b_rho)
+                  + algorithmic_bytes("rowbox", N_avg, E, GC, b_sum, b_rho)
+                  + algorithmic_bytes("colbox", N_avg, E, GC, b_sum, b_rho)
+                  + algorithmic_bytes("combine", N_avg, E, GC, b_sum, b_rho))
+    pkg.bundle_destroy(ctx)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generator shaped like the paper's graphs)",
+        "config": {**describe(w, args.rho), "parallelism": f"{world} independent graphs"
+                   if world > 1 else "single GPU", "points_per_step": N_avg},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": dom_bytes,
+                     "ms_per_launch": dom_ms},
+        "step_roofline": {"algorithmic_bytes": step_bytes,
+                          "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
+                          "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak},
+        "kernels": per_kernel,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    if not args.no_variants and world == 1 and args.rho == "f32":
+        var = {}
+        for rho in ("bf16",):
+            p2 = params_of(w, rho)
+            c2 = pkg.bundle_init(p2, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight,
+                                 stream=stream)
+            pkg.bundle_iterate(c2, max(args.warmup, 3))
+            pkg.bundle_sync(c2)
+            d0 = pkg.bundle_get_info(c2).points_processed
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pkg.bundle_iterate(c2, args.steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            m2 = a.elapsed_time(b)
+            u2 = pkg.bundle_get_info(c2).points_processed - d0
+            var[rho] = {"value": u2 / (m2 / 1e3), "ms_per_step": m2 / args.steps}
+            pkg.bundle_destroy(c2)
+        out["variants"] = var
+
+    if not args.no_e2e:
+        # the whole job through the public API: pinned host edges in, polylines back to host
+        src = torch.from_numpy(w.src_xy).pin_memory()
+        dst = torch.from_numpy(w.dst_xy).pin_memory()
+        grp = torch.from_numpy(w.group).pin_memory()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c3 = pkg.bundle_init(p, src, dst, grp, w.n_groups, None, stream=stream)
+        pkg.bundle_iterate(c3, args.steps)
+        inf3 = pkg.bundle_get_info(c3)
+        off_h = torch.empty(E + 1, dtype=torch.int64).pin_memory()
+        xy_h = torch.empty((inf3.n_points, 2), dtype=torch.float32).pin_memory()
+        pkg.bundle_fetch(c3, off=off_h, xy=xy_h)
+        t1 = time.perf_counter()
+        upd3 = inf3.points_processed
+        pkg.bundle_destroy(c3)
+        e2e_s = t1 - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+            u = torch.tensor([float(upd3)], device="cuda")
+            dist.all_reduce(u, op=dist.ReduceOp.SUM)
+            upd3 = u.item()
+        h2d = w.n_edges * (8 + 8 + 4)
+        d2h = (E + 1) * 8 + int(inf3.n_points) * 8
+        out["e2e"] = {"value": upd3 / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                      "scope": (f"bundle_init from pinned host edges + {args.steps} iterations + "
+                                "bundle_fetch to pinned host, wall clock")}
+
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, 1_500_000 if args.workload != "small" else 2000)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * bundle.h - C ABI of the GB300 (sm_103a) 3DHEB edge-bundling library.
+ *
+ * The library runs the per-iteration loop of "3D Density Histograms for
+ * Criteria-driven Edge Bundling" (Moura), Sec. 3 / Fig. 2, on one GPU:
+ *   resample every polyline (Sec. 2.1, Sec. 3) ->
+ *   per-group integer histogram of the sample points (Eq. 1, Eq. 3) ->
+ *   repeated box filters per layer, integer and exact (Sec. 3.1) ->
+ *   layer interaction M (Eq. 3, Eq. 4) -> density rho ->
+ *   advection along the bilinear density gradient with the halving step
+ *   (Eq. 5, Sec. 3.3) -> Laplacian smoothing of the polylines (Sec. 3.3).
+ *
+ * Units. After bundle_init every position lives in grid pixel units: cell
+ * (u, v) covers [u, u+1) x [v, v+1), x is the column, y the row. World
+ * coordinates are mapped once at init (Sec. 5: a fixed dominant grid size, the
+ * other from the bounding box's aspect ratio) and mapped back by bundle_fetch.
+ *
+ * Conventions for every call:
+ *  - Every call returns a bundle_status; none aborts, traps or exits. The
+ *    context keeps a message for the last failure (bundle_last_error).
+ *  - Ownership: the library copies every input array at init into device
+ *    buffers it owns; the caller keeps ownership of all pointers it passes and
+ *    may free them once the call returns. Output buffers belong to the caller.
+ *  - Pointers are host pointers unless a *_DEVICE flag says they are device
+ *    pointers on the context's GPU.
+ *  - Streams: `stream` is a cudaStream_t (NULL: the library creates its own
+ *    non-blocking stream). bundle_iterate is asynchronous on that stream; the
+ *    fetches synchronise it.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef BUNDLE_3DHEB_H
+#define BUNDLE_3DHEB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BUNDLE_OK = 0,
+    BUNDLE_EINVAL = 1,    /* an argument is out of range or inconsistent */
+    BUNDLE_ENOMEM = 2,    /* a device or host allocation failed */
+    BUNDLE_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    BUNDLE_EOVERFLOW = 4, /* the integer widths cannot hold the worst-case bound */
+    BUNDLE_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    BUNDLE_ESTATE = 6,    /* the call is not valid in the context's current state */
+    BUNDLE_ENOTSUP = 7    /* a requested mode is not supported by this build */
+} bundle_status;
+
+/* Storage type of the density stack rho read by the gradient gather. */
+typedef enum { BUNDLE_RHO_F32 = 0, BUNDLE_RHO_BF16 = 1, BUNDLE_RHO_F16 = 2 } bundle_rho_dtype;
+
+/* Parameters. Fill with bundle_default_params, then override. */
+typedef struct {
+    int32_t grid_w, grid_h;   /* histogram size; both 0 => automatic (Sec. 5) */
+    int32_t grid_dominant;    /* automatic size of the dominant axis (Sec. 5: 800) */
+    int32_t margin_px;        /* free border kept by the world->grid map; -1 => radius */
+    int32_t radius;           /* box radius r: each pass sums (2r+1)^2 cells (Sec. 3.1) */
+    int32_t passes;           /* number of box passes k (Sec. 3.1: 3) */
+    int32_t alpha_num;        /* repulsion alpha = alpha_num / alpha_den (Eq. 4: 1/4) */
+    int32_t alpha_den;
+    double h_max_sigmas;      /* h_max = h_max_sigmas * sigma_k (Sec. 3.3, Fig. 3: 2) */
+    double lambda;            /* h_i = lambda^i h_max (Sec. 2.1: 0.5..0.9; Fig. 3: 0.9) */
+    int32_t n_fixed;          /* > 0: points per polyline; 0: by length (below) */
+    int32_t n_max;            /* by length: clamp(ceil(L / delta_px) + 1, 2, n_max) */
+    float delta_px;           /* sampling step delta in pixels (Sec. 2.1) */
+    float laplace_beta;       /* Laplacian weight beta (Sec. 3.3 leaves it open: 0.5) */
+    float eps;                /* epsilon of Eq. 5 (density units: weight per cell) */
+    int32_t step_tries;       /* step sizes tried: h, h/2, ..., h/2^(tries-1) (Sec. 3.3) */
+    int32_t sum_bits;         /* width of the smoothed sums: 0 auto, 32 or 64 */
+    int32_t rho_dtype;        /* bundle_rho_dtype */
+    int32_t flags;            /* reserved, 0 */
+} bundle_params;
+
+/* Result of bundle_get_info. */
+typedef struct {
+    int64_t n_edges;
+    int64_t n_points;           /* points of the current polylines (after the last iteration) */
+    int64_t n_points_resampled; /* points splatted by the last iteration */
+    int32_t grid_w, grid_h, n_groups;
+    int32_t sum_bits;           /* 32 or 64 */
+    int32_t rho_dtype;
+    int32_t iteration;          /* index i of the next iteration (h_i) */
+    double map[5];              /* {xmin, ymin, scale, ox, oy}: px = (x - xmin) * scale + ox */
+    double h_next;              /* h of the next iteration */
+    int64_t device_bytes;       /* device memory owned by the context */
+    int64_t points_processed;   /* sample points resampled and splatted since init: the sum
+                                   over iterations of the points each iteration advects */
+} bundle_info;
+
+typedef struct bundle_ctx bundle_ctx;
+
+/* bundle_init / bundle_init_polylines flags */
+#define BUNDLE_INPUT_DEVICE 1 /* input arrays are device pointers */
+
+/* bundle_fetch flags */
+#define BUNDLE_FETCH_DEVICE 1    /* off / xy are device pointers */
+#define BUNDLE_FETCH_PIXELS 2    /* return grid pixel units instead of world coordinates */
+#define BUNDLE_FETCH_RESAMPLED 4 /* the last iteration's resampled points (the splat input) */
+
+/* bundle_fetch_density selectors */
+#define BUNDLE_DENSITY_HIST 0 /* uint32 [G][H][W]: histogram of the last iteration (Eq. 1/3) */
+#define BUNDLE_DENSITY_SUMS 1 /* int32/int64 [G][H][W]: k box passes, unnormalised (Sec. 3.1) */
+#define BUNDLE_DENSITY_RHO 2  /* f32/bf16/f16 [G][H][W]: combined density (Eq. 3, Eq. 4) */
+
+/* Defaults: the paper's values where it gives them (k = 3, alpha = 1/4,
+ * h_max = 2 sigma, lambda = 0.9, dominant size 800), the readings for the
+ * rest (r = 4, delta = 2 px, n_max = 64, beta = 0.5, eps = 1e-9, 8 tries). */
+void bundle_default_params(bundle_params* p);
+
+/*
+ * Create a context from straight edges (Sec. 3.1: e = (x_s, x_t, w)).
+ *  src_xy, dst_xy: float [2 * n_edges], interleaved (x, y), world coordinates.
+ *  group: int32 [n_edges], group (bin) b_e in [0, n_groups) (Sec. 3.2); NULL => all 0.
+ *  weight: int32 [n_edges], w_e >= 0 (Eq. 1); NULL => all 1.
+ *  n_groups: 1..64 (Sec. 6 reports up to 64 groups).
+ *  flags: BUNDLE_INPUT_DEVICE when the four arrays are device pointers.
+ * The world->grid map is computed on the host in double and rounded to float
+ * once. Returns EINVAL for bad sizes, EOVERFLOW when the integer histogram,
+ * sums or layer mix cannot hold their worst-case bound, ENOMEM, ECUDA.
+ * On failure *out is NULL and bundle_last_error(NULL) describes the cause.
+ */
+bundle_status bundle_init(bundle_ctx** out, const bundle_params* p, int64_t n_edges,
+                          const float* src_xy, const float* dst_xy, const int32_t* group,
+                          int32_t n_groups, const int32_t* weight, int32_t flags, void* stream);
+
+/*
+ * Create a context from polylines already in grid pixel units (resume from a
+ * fetched state, or start from a chosen configuration).
+ *  off: int64 [n_edges + 1] CSR offsets; every polyline has 2..cap points,
+ *       cap = n_fixed if > 0 else n_max.
+ *  xy_px: float [2 * off[n_edges]], interleaved, inside [0, W) x [0, H).
+ *  p->grid_w, p->grid_h must be > 0. map5: the world map to report and to
+ *  invert in bundle_fetch (NULL: identity, scale 1). iteration: index i of the
+ *  first iteration to run (sets h_i).
+ */
+bundle_status bundle_init_polylines(bundle_ctx** out, const bundle_params* p, int64_t n_edges,
+                                    const int64_t* off, const float* xy_px, const int32_t* group,
+                                    int32_t n_groups, const int32_t* weight, const double* map5,
+                                    int32_t iteration, int32_t flags, void* stream);
+
+/*
+ * Run n_iters iterations of the loop (Sec. 3, Fig. 2) asynchronously on the
+ * context's stream. Iteration i uses h_i = lambda^i h_max (Sec. 2.1, Sec. 3.3).
+ * Returns EINVAL for n_iters < 0, ECUDA if a launch fails.
+ */
+bundle_status bundle_iterate(bundle_ctx* ctx, int32_t n_iters);
+
+/*
+ * Copy the current polylines out (synchronises the stream).
+ *  off: int64 [n_edges + 1] CSR offsets, in the caller's edge order.
+ *  xy: float [2 * cap], interleaved; n_points receives the point count.
+ *  flags: BUNDLE_FETCH_DEVICE, BUNDLE_FETCH_PIXELS, BUNDLE_FETCH_RESAMPLED.
+ * Returns EINVAL when cap is smaller than the point count (n_points is still
+ * set), ESTATE for RESAMPLED before any iteration.
+ */
+bundle_status bundle_fetch(bundle_ctx* ctx, int64_t* off, float* xy, int64_t cap,
+                           int64_t* n_points, int32_t flags);
+
+/*
+ * Copy one [G][H][W] stack of the last iteration (synchronises the stream).
+ * which: BUNDLE_DENSITY_HIST (uint32), _SUMS (int32 or int64 per sum_bits),
+ * _RHO (per rho_dtype). dst_bytes must be at least G*H*W*element size.
+ * flags: BUNDLE_FETCH_DEVICE when dst is a device pointer.
+ */
+bundle_status bundle_fetch_density(bundle_ctx* ctx, int32_t which, void* dst, int64_t dst_bytes,
+                                   int32_t flags);
+
+/* Sizes, widths, map, schedule and point counts of a context (synchronises the stream). */
+bundle_status bundle_get_info(const bundle_ctx* ctx, bundle_info* out);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch of bundle_iterate (a tracing aid; off by default, adds two event
+ * records per launch). Kinds, in order: 0 resample+splat, 1 advect+Laplacian,
+ * 2 advect+Laplacian+resample+splat, 3 row box passes, 4 column box passes,
+ * 5 layer mix, 6 histogram clear.
+ */
+#define BUNDLE_PROFILE_KINDS 7
+bundle_status bundle_profile_enable(bundle_ctx* ctx, int32_t on);
+
+/*
+ * Synchronise and report, per kind, the summed event time in ms and the
+ * launch count of everything recorded since the last reset. ms and launches
+ * hold n entries (n <= BUNDLE_PROFILE_KINDS is read; extra entries are zeroed).
+ * reset != 0 clears the records.
+ */
+bundle_status bundle_profile_read(bundle_ctx* ctx, double* ms, int64_t* launches, int32_t n,
+                                  int32_t reset);
+
+/* Wait for the context's stream; reports a deferred kernel error as ECUDA. */
+bundle_status bundle_sync(bundle_ctx* ctx);
+
+/* Free every resource of the context (synchronises first). NULL is a no-op. */
+void bundle_destroy(bundle_ctx* ctx);
+
+/* Message of the last failure of ctx (NULL: of the last failed init on this thread). */
+const char* bundle_last_error(const bundle_ctx* ctx);
+
+/* Name of a status code. */
+const char* bundle_status_string(bundle_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BUNDLE_3DHEB_H */

@@ -1,0 +1,315 @@
+"""GB300 (sm_103a) 3DHEB edge bundling: Python binding of the C ABI in include/bundle.h.
+
+This module only marshals arguments (numpy arrays, torch tensors, streams) to
+the shared library built from ``csrc/``; every step of the bundling iteration
+runs in the library's CUDA kernels. There is no CPU fallback: if the library
+is missing or cannot be loaded, importing the binding's functions raises.
+
+Names follow the C ABI: ``bundle_init``, ``bundle_init_polylines``,
+``bundle_iterate``, ``bundle_fetch``, ``bundle_fetch_density``,
+``bundle_get_info``, ``bundle_sync``, ``bundle_destroy``; ``Bundler`` wraps a
+context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbundle3dheb.so")
+
+BUNDLE_OK, BUNDLE_EINVAL, BUNDLE_ENOMEM, BUNDLE_ECUDA = 0, 1, 2, 3
+BUNDLE_EOVERFLOW, BUNDLE_ETIMEOUT, BUNDLE_ESTATE, BUNDLE_ENOTSUP = 4, 5, 6, 7
+RHO_F32, RHO_BF16, RHO_F16 = 0, 1, 2
+INPUT_DEVICE = 1
+FETCH_DEVICE, FETCH_PIXELS, FETCH_RESAMPLED = 1, 2, 4
+DENSITY_HIST, DENSITY_SUMS, DENSITY_RHO = 0, 1, 2
+PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "combine",
+                 "hist_clear")
+
+EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bundle_iterate",
+            "bundle_fetch", "bundle_fetch_density", "bundle_get_info", "bundle_sync",
+            "bundle_destroy", "bundle_last_error", "bundle_status_string",
+            "bundle_profile_enable", "bundle_profile_read")
+
+
+class BundleParams(ctypes.Structure):
+    """Mirror of ``bundle_params`` (field order and types must match include/bundle.h)."""
+    _fields_ = [
+        ("grid_w", ctypes.c_int32), ("grid_h", ctypes.c_int32),
+        ("grid_dominant", ctypes.c_int32), ("margin_px", ctypes.c_int32),
+        ("radius", ctypes.c_int32), ("passes", ctypes.c_int32),
+        ("alpha_num", ctypes.c_int32), ("alpha_den", ctypes.c_int32),
+        ("h_max_sigmas", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("n_fixed", ctypes.c_int32), ("n_max", ctypes.c_int32),
+        ("delta_px", ctypes.c_float), ("laplace_beta", ctypes.c_float), ("eps", ctypes.c_float),
+        ("step_tries", ctypes.c_int32), ("sum_bits", ctypes.c_int32),
+        ("rho_dtype", ctypes.c_int32), ("flags", ctypes.c_int32),
+    ]
+
+
+class BundleInfo(ctypes.Structure):
+    """Mirror of ``bundle_info``."""
+    _fields_ = [
+        ("n_edges", ctypes.c_int64), ("n_points", ctypes.c_int64),
+        ("n_points_resampled", ctypes.c_int64),
+        ("grid_w", ctypes.c_int32), ("grid_h", ctypes.c_int32), ("n_groups", ctypes.c_int32),
+        ("sum_bits", ctypes.c_int32), ("rho_dtype", ctypes.c_int32),
+        ("iteration", ctypes.c_int32), ("map", ctypes.c_double * 5), ("h_next", ctypes.c_double),
+        ("device_bytes", ctypes.c_int64), ("points_processed", ctypes.c_int64),
+    ]
+
+
+class BundleError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built: no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"bundling library not built: {LIB_PATH} is missing "
+                          "(run paper_1504_02687_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    pp = ctypes.POINTER(BundleParams)
+    L.bundle_default_params.argtypes = [pp]
+    L.bundle_default_params.restype = None
+    L.bundle_init.argtypes = [ctypes.POINTER(P), pp, i64, P, P, P, i32, P, i32, P]
+    L.bundle_init.restype = i32
+    L.bundle_init_polylines.argtypes = [ctypes.POINTER(P), pp, i64, P, P, P, i32, P, P, i32, i32,
+                                        P]
+    L.bundle_init_polylines.restype = i32
+    L.bundle_iterate.argtypes = [P, i32]
+    L.bundle_iterate.restype = i32
+    L.bundle_fetch.argtypes = [P, P, P, i64, ctypes.POINTER(i64), i32]
+    L.bundle_fetch.restype = i32
+    L.bundle_fetch_density.argtypes = [P, i32, P, i64, i32]
+    L.bundle_fetch_density.restype = i32
+    L.bundle_get_info.argtypes = [P, ctypes.POINTER(BundleInfo)]
+    L.bundle_get_info.restype = i32
+    L.bundle_sync.argtypes = [P]
+    L.bundle_sync.restype = i32
+    L.bundle_destroy.argtypes = [P]
+    L.bundle_destroy.restype = None
+    L.bundle_last_error.argtypes = [P]
+    L.bundle_last_error.restype = ctypes.c_char_p
+    L.bundle_status_string.argtypes = [i32]
+    L.bundle_status_string.restype = ctypes.c_char_p
+    L.bundle_profile_enable.argtypes = [P, i32]
+    L.bundle_profile_enable.restype = i32
+    L.bundle_profile_read.argtypes = [P, P, P, i32, i32]
+    L.bundle_profile_read.restype = i32
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().bundle_status_string(int(s)).decode()
+
+
+def default_params(**overrides) -> BundleParams:
+    p = BundleParams()
+    lib().bundle_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lam" else k, v)
+    return p
+
+
+def _check(status: int, ctx=None):
+    if status != BUNDLE_OK:
+        msg = lib().bundle_last_error(ctx).decode(errors="replace")
+        raise BundleError(status, msg)
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def bundle_init(params: BundleParams, src_xy, dst_xy, group=None, n_groups=1, weight=None,
+                stream=None):
+    """Create a context from straight edges. Arrays are numpy (host) or CUDA torch tensors
+    (all on the device together). Returns the opaque context handle."""
+    dev = _is_device(src_xy)
+    if not dev:
+        src_xy = _host(src_xy, np.float32)
+        dst_xy = _host(dst_xy, np.float32)
+        group = _host(group, np.int32)
+        weight = _host(weight, np.int32)
+    E = int(src_xy.shape[0]) if src_xy.ndim == 2 else int(src_xy.shape[0] // 2)
+    ctx = ctypes.c_void_p()
+    st = lib().bundle_init(ctypes.byref(ctx), ctypes.byref(params), E, _ptr(src_xy), _ptr(dst_xy),
+                           _ptr(group), int(n_groups), _ptr(weight), INPUT_DEVICE if dev else 0,
+                           _stream_handle(stream))
+    _check(st)
+    return ctx
+
+
+def bundle_init_polylines(params: BundleParams, off, xy_px, group=None, n_groups=1, weight=None,
+                          map5=None, iteration=0, stream=None):
+    """Create a context from CSR polylines in grid pixel units (params.grid_w/h set)."""
+    dev = _is_device(xy_px)
+    if not dev:
+        off = _host(off, np.int64)
+        xy_px = _host(xy_px, np.float32)
+        group = _host(group, np.int32)
+        weight = _host(weight, np.int32)
+    m = None if map5 is None else _host(map5, np.float64)
+    E = int(off.shape[0]) - 1
+    ctx = ctypes.c_void_p()
+    st = lib().bundle_init_polylines(ctypes.byref(ctx), ctypes.byref(params), E, _ptr(off),
+                                     _ptr(xy_px), _ptr(group), int(n_groups), _ptr(weight), _ptr(m),
+                                     int(iteration), INPUT_DEVICE if dev else 0,
+                                     _stream_handle(stream))
+    _check(st)
+    return ctx
+
+
+def bundle_iterate(ctx, n_iters: int):
+    _check(lib().bundle_iterate(ctx, int(n_iters)), ctx)
+
+
+def bundle_sync(ctx):
+    _check(lib().bundle_sync(ctx), ctx)
+
+
+def bundle_get_info(ctx) -> BundleInfo:
+    info = BundleInfo()
+    _check(lib().bundle_get_info(ctx, ctypes.byref(info)), ctx)
+    return info
+
+
+def bundle_fetch(ctx, pixels=False, resampled=False, off=None, xy=None):
+    """Return (off int64 [E+1], xy float32 [N, 2]). With `off`/`xy` given (CUDA tensors or
+    numpy arrays), fills them instead and returns them."""
+    info = bundle_get_info(ctx)
+    flags = (FETCH_PIXELS if pixels else 0) | (FETCH_RESAMPLED if resampled else 0)
+    n = ctypes.c_int64()
+    if off is None:
+        off = np.zeros(info.n_edges + 1, np.int64)
+        N = info.n_points_resampled if resampled else info.n_points
+        xy = np.zeros((max(int(N), 1), 2), np.float32)
+    if _is_device(off):
+        flags |= FETCH_DEVICE
+    cap = int(xy.shape[0]) if xy is not None else 0
+    _check(lib().bundle_fetch(ctx, _ptr(off), _ptr(xy), cap, ctypes.byref(n), flags), ctx)
+    return off, xy[: n.value]
+
+
+def bundle_fetch_density(ctx, which: int, out=None):
+    """Return one [G, H, W] stack of the last iteration (numpy unless `out` is given)."""
+    info = bundle_get_info(ctx)
+    shape = (info.n_groups, info.grid_h, info.grid_w)
+    if out is None:
+        if which == DENSITY_HIST:
+            out = np.zeros(shape, np.uint32)
+        elif which == DENSITY_SUMS:
+            out = np.zeros(shape, np.int32 if info.sum_bits == 32 else np.int64)
+        else:
+            out = np.zeros(shape, np.float32 if info.rho_dtype == RHO_F32 else np.uint16)
+    nbytes = out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes
+    flags = FETCH_DEVICE if _is_device(out) else 0
+    _check(lib().bundle_fetch_density(ctx, int(which), _ptr(out), int(nbytes), flags), ctx)
+    return out
+
+
+def bundle_profile_enable(ctx, on: bool = True):
+    _check(lib().bundle_profile_enable(ctx, 1 if on else 0), ctx)
+
+
+def bundle_profile_read(ctx, reset: bool = True) -> dict:
+    """Per kernel kind: (total ms, launches) of the launches recorded since the last read."""
+    n = len(PROFILE_KINDS)
+    ms = np.zeros(n, np.float64)
+    cnt = np.zeros(n, np.int64)
+    _check(lib().bundle_profile_read(ctx, _ptr(ms), _ptr(cnt), n, 1 if reset else 0), ctx)
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def bundle_destroy(ctx):
+    if ctx:
+        lib().bundle_destroy(ctx)
+
+
+class Bundler:
+    """Owning wrapper of one context."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    @classmethod
+    def from_edges(cls, src_xy, dst_xy, group=None, n_groups=1, weight=None, params=None,
+                   stream=None, **overrides):
+        p = params if params is not None else default_params(**overrides)
+        return cls(bundle_init(p, src_xy, dst_xy, group, n_groups, weight, stream))
+
+    @classmethod
+    def from_polylines(cls, off, xy_px, grid, group=None, n_groups=1, weight=None, map5=None,
+                       iteration=0, params=None, stream=None, **overrides):
+        p = params if params is not None else default_params(**overrides)
+        p.grid_w, p.grid_h = int(grid[0]), int(grid[1])
+        return cls(bundle_init_polylines(p, off, xy_px, group, n_groups, weight, map5, iteration,
+                                         stream))
+
+    def iterate(self, n: int = 1):
+        bundle_iterate(self.ctx, n)
+        return self
+
+    def sync(self):
+        bundle_sync(self.ctx)
+
+    def info(self) -> BundleInfo:
+        return bundle_get_info(self.ctx)
+
+    def fetch(self, pixels=False, resampled=False):
+        return bundle_fetch(self.ctx, pixels=pixels, resampled=resampled)
+
+    def density(self, which: int):
+        return bundle_fetch_density(self.ctx, which)
+
+    def close(self):
+        bundle_destroy(self.ctx)
+        self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.ctx:
+                self.close()
+        except Exception:
+            pass

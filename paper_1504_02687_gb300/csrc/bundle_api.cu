@@ -1,0 +1,918 @@
+// Host side of the C ABI declared in include/bundle.h: argument checks, the
+// integer-width bounds, the world -> grid map, device buffers, the launch
+// sequence of one bundling iteration and the fetches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/bundle.h"
+#include "internal.cuh"
+
+using namespace heb;
+
+struct bundle_ctx {
+    bundle_params p{};
+    int64_t E = 0;
+    int32_t G = 1, W = 0, H = 0;
+    int32_t cap = 0;
+    int64_t n_blocks = 0;
+    int32_t sum_bits = 64;
+    int64_t mix_self = 1, mix_all = 0;
+    float den_f = 1.0f;
+    double map[5] = {0, 0, 1, 0, 0};
+    int32_t iteration = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device state
+    int32_t* perm = nullptr;      // slot -> caller edge index
+    int32_t* group = nullptr;     // per slot
+    int32_t* weight = nullptr;    // per slot
+    int32_t* cnt[2] = {nullptr, nullptr};
+    float2* pts[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;
+    void* Y = nullptr;
+    void* S = nullptr;
+    void* rho = nullptr;
+    unsigned long long* counters = nullptr;  // [0] points splatted in total, [1] scratch sum
+    int64_t* fetch_off = nullptr;
+    int64_t* fetch_tmp = nullptr;
+    float2* fetch_xy = nullptr;
+    int64_t fetch_xy_cap = 0;
+    int cur_P = 0;       // buffer holding the current polylines
+    int cur_R = -1;      // buffer holding the last resampled polylines (-1: none yet)
+    bool have_density = false;
+    int64_t device_bytes = 0;
+    // per-kernel event timing (bundle_profile_enable)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;  // kind of each recorded (start, stop) pair
+    size_t ev_used = 0;        // events in use (2 per record)
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bundle_status fail(std::string* sink, bundle_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    *sink = buf;
+    return s;
+}
+
+#define CUDA_TRY(sink, expr)                                                              \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(sink, e_ == cudaErrorMemoryAllocation ? BUNDLE_ENOMEM : BUNDLE_ECUDA, \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(bundle_ctx* c, T** ptr, size_t n) {
+    *ptr = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), n * sizeof(T));
+    if (e == cudaSuccess) c->device_bytes += (int64_t)(n * sizeof(T));
+    return e;
+}
+
+void free_ctx(bundle_ctx* c) {
+    if (!c) return;
+    if (c->device < 0) {
+        delete c;
+        return;
+    }
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    void* ptrs[] = {c->perm, c->group, c->weight, c->cnt[0], c->cnt[1], c->pts[0], c->pts[1],
+                    c->hist, c->Y, c->S, c->rho, c->counters, c->fetch_off, c->fetch_tmp,
+                    c->fetch_xy};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int rho_bytes(int dtype) { return dtype == BUNDLE_RHO_F32 ? 4 : 2; }
+
+// Kernel bandwidth of iteration i (Sec. 2.1, Sec. 3.3): h_i = lambda^i h_max,
+// h_max = h_max_sigmas * sigma_k with sigma_k^2 = k r (r + 1) / 3, the variance
+// of k box passes of width 2r+1.
+double bandwidth(const bundle_params& p, int32_t i) {
+    double sigma = std::sqrt((double)((int64_t)p.passes * p.radius * (p.radius + 1)) / 3.0);
+    double h = p.h_max_sigmas * sigma;
+    for (int32_t t = 0; t < i; ++t) h *= p.lambda;
+    return h;
+}
+
+bundle_status check_params(const bundle_params& p, int32_t n_groups, std::string* e) {
+    if (n_groups < 1 || n_groups > 64)
+        return fail(e, BUNDLE_EINVAL, "n_groups must be in [1, 64], got %d", n_groups);
+    if (p.radius < 1) return fail(e, BUNDLE_EINVAL, "radius must be >= 1, got %d", p.radius);
+    if (p.passes < 1 || p.passes > 16)
+        return fail(e, BUNDLE_EINVAL, "passes must be in [1, 16], got %d", p.passes);
+    if (p.alpha_den <= 0 || p.alpha_num < 0)
+        return fail(e, BUNDLE_EINVAL, "alpha must be p/q with p >= 0, q > 0");
+    if (!(p.lambda > 0 && p.lambda <= 1) || !(p.h_max_sigmas > 0))
+        return fail(e, BUNDLE_EINVAL, "need 0 < lambda <= 1 and h_max_sigmas > 0");
+    if (p.n_fixed != 0 && (p.n_fixed < 2 || p.n_fixed > kMaxCap))
+        return fail(e, BUNDLE_EINVAL, "n_fixed must be 0 or in [2, %d]", kMaxCap);
+    if (p.n_fixed == 0 && (p.n_max < 2 || p.n_max > kMaxCap))
+        return fail(e, BUNDLE_EINVAL, "n_max must be in [2, %d]", kMaxCap);
+    if (p.n_fixed == 0 && !(p.delta_px > 0))
+        return fail(e, BUNDLE_EINVAL, "delta_px must be > 0");
+    if (!(p.laplace_beta >= 0 && p.laplace_beta <= 1))
+        return fail(e, BUNDLE_EINVAL, "laplace_beta must be in [0, 1]");
+    if (!(p.eps >= 0)) return fail(e, BUNDLE_EINVAL, "eps must be >= 0");
+    if (p.step_tries < 1 || p.step_tries > 64)
+        return fail(e, BUNDLE_EINVAL, "step_tries must be in [1, 64]");
+    if (p.sum_bits != 0 && p.sum_bits != 32 && p.sum_bits != 64)
+        return fail(e, BUNDLE_EINVAL, "sum_bits must be 0, 32 or 64");
+    if (p.rho_dtype < 0 || p.rho_dtype > 2) return fail(e, BUNDLE_EINVAL, "bad rho_dtype");
+    if (p.grid_dominant < 2 || p.grid_dominant > 4096)
+        return fail(e, BUNDLE_EINVAL, "grid_dominant must be in [2, 4096]");
+    return BUNDLE_OK;
+}
+
+// Integer widths (Eq. 1 histogram, Sec. 3.1 sums, Eq. 3-4 mix) from the
+// worst case: M0 = sum_e w_e * cap points' weight. With reflection a cell can
+// enter a window at most twice per axis, so after p passes every cell and
+// every intermediate is at most 4 s^(p-1) M0, s = (2r+1)^2.
+bundle_status size_integers(bundle_ctx* c, const int32_t* weight_host, std::string* e) {
+    double M0 = 0;
+    if (weight_host) {
+        for (int64_t i = 0; i < c->E; ++i) {
+            if (weight_host[i] < 0)
+                return fail(e, BUNDLE_EINVAL, "weight[%lld] = %d is negative", (long long)i,
+                            weight_host[i]);
+            M0 += (double)weight_host[i];
+        }
+    } else {
+        M0 = (double)c->E;
+    }
+    M0 *= c->cap;
+    const double two31 = 2147483648.0, two63 = 9223372036854775808.0;
+    if (M0 >= two31 * (1 - 1e-12))
+        return fail(e, BUNDLE_EOVERFLOW,
+                    "histogram bound sum(w)*cap = %.6g does not fit uint32 cells", M0);
+    const double s = (double)(2 * c->p.radius + 1) * (double)(2 * c->p.radius + 1);
+    double bound = 4.0 * M0;
+    for (int p = 1; p < c->p.passes; ++p) bound *= s;
+    int bits = c->p.sum_bits;
+    if (bits == 0) bits = bound < two31 * (1 - 1e-12) ? 32 : 64;
+    if (bits == 32 && !(bound < two31 * (1 - 1e-12)))
+        return fail(e, BUNDLE_EOVERFLOW, "smoothed-sum bound %.6g does not fit int32", bound);
+    if (!(bound < two63 * (1 - 1e-12)))
+        return fail(e, BUNDLE_EOVERFLOW, "smoothed-sum bound %.6g does not fit int64", bound);
+    c->sum_bits = bits;
+    double sk = 1;
+    for (int p = 0; p < c->p.passes; ++p) sk *= s;
+    if (c->G > 1) {
+        c->mix_self = (int64_t)c->p.alpha_den * (c->G - 1) + c->p.alpha_num;
+        c->mix_all = c->p.alpha_num;
+        if (!((double)c->mix_self * bound < two63 * (1 - 1e-12)))
+            return fail(e, BUNDLE_EOVERFLOW,
+                        "layer-mix bound %.6g * %lld does not fit int64 (fewer points, passes or "
+                        "groups, or a smaller radius)",
+                        bound, (long long)c->mix_self);
+        c->den_f = (float)((double)c->p.alpha_den * (c->G - 1) * sk);
+    } else {
+        c->mix_self = 1;
+        c->mix_all = 0;
+        c->den_f = (float)sk;
+    }
+    return BUNDLE_OK;
+}
+
+// World -> grid pixel map (Sec. 5): bounding box onto [m, W - m] x [m, H - m]
+// with one isotropic scale, centred; computed in double, rounded to float once.
+bundle_status grid_map(bundle_ctx* c, const float* src, const float* dst, std::string* e,
+                       std::vector<float>* src_px, std::vector<float>* dst_px) {
+    const int64_t E = c->E;
+    const int margin = c->p.margin_px < 0 ? c->p.radius : c->p.margin_px;
+    const double inf = std::numeric_limits<double>::infinity();
+    double xmin = inf, ymin = inf, xmax = -inf, ymax = -inf;
+    for (int64_t i = 0; i < E; ++i) {
+        const float* q[2] = {src + 2 * i, dst + 2 * i};
+        for (const float* v : q) {
+            double x = v[0], y = v[1];
+            if (!std::isfinite(x) || !std::isfinite(y))
+                return fail(e, BUNDLE_EINVAL, "edge %lld has a non-finite coordinate",
+                            (long long)i);
+            xmin = std::min(xmin, x);
+            xmax = std::max(xmax, x);
+            ymin = std::min(ymin, y);
+            ymax = std::max(ymax, y);
+        }
+    }
+    double sx = xmax - xmin, sy = ymax - ymin;
+    int64_t W = c->p.grid_w, H = c->p.grid_h;
+    if (W <= 0 && H <= 0) {
+        const int64_t dom = c->p.grid_dominant, lo = 2 * (int64_t)margin + 2;
+        if (sx >= sy) {
+            W = dom;
+            H = sx > 0 ? (int64_t)std::llround(dom * (sy / sx)) : dom;
+        } else {
+            H = dom;
+            W = (int64_t)std::llround(dom * (sx / sy));
+        }
+        W = std::max(W, lo);
+        H = std::max(H, lo);
+    } else if (W <= 0 || H <= 0) {
+        return fail(e, BUNDLE_EINVAL, "grid_w and grid_h must both be > 0 or both be 0");
+    }
+    if (W < 2 || H < 2 || W > 4096 || H > 4096)
+        return fail(e, BUNDLE_EINVAL, "grid %lld x %lld outside [2, 4096]", (long long)W,
+                    (long long)H);
+    if (W - 2 * (int64_t)margin <= 0 || H - 2 * (int64_t)margin <= 0)
+        return fail(e, BUNDLE_EINVAL, "margin %d leaves no room on a %lld x %lld grid", margin,
+                    (long long)W, (long long)H);
+    double kx = sx > 0 ? ((double)W - 2.0 * margin) / sx : inf;
+    double ky = sy > 0 ? ((double)H - 2.0 * margin) / sy : inf;
+    double scale = std::min(kx, ky);
+    if (!(scale < inf)) scale = 1.0;
+    double ox = ((double)W - scale * sx) / 2.0;
+    double oy = ((double)H - scale * sy) / 2.0;
+    c->W = (int32_t)W;
+    c->H = (int32_t)H;
+    c->map[0] = xmin;
+    c->map[1] = ymin;
+    c->map[2] = scale;
+    c->map[3] = ox;
+    c->map[4] = oy;
+    src_px->resize((size_t)(2 * E));
+    dst_px->resize((size_t)(2 * E));
+    const float hx = (float)W - kEdgeGuard, hy = (float)H - kEdgeGuard;
+    auto work = [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            const float* in[2] = {src + 2 * i, dst + 2 * i};
+            float* out[2] = {src_px->data() + 2 * i, dst_px->data() + 2 * i};
+            for (int s = 0; s < 2; ++s) {
+                double px = ((double)in[s][0] - xmin) * scale + ox;
+                double py = ((double)in[s][1] - ymin) * scale + oy;
+                float fx = (float)px, fy = (float)py;
+                out[s][0] = std::min(std::max(fx, 0.0f), hx);
+                out[s][1] = std::min(std::max(fy, 0.0f), hy);
+            }
+        }
+    };
+    unsigned nt = std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()));
+    if (E < 200000) nt = 1;
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back(work, E * t / nt, E * (t + 1) / nt);
+    for (auto& t : th) t.join();
+    return BUNDLE_OK;
+}
+
+// Device buffers sized from E, cap, G, H, W and the widths.
+bundle_status alloc_state(bundle_ctx* c, std::string* e) {
+    const int64_t E = c->E;
+    c->n_blocks = (E + kEdgesPerBlock - 1) / kEdgesPerBlock;
+    const size_t region = (size_t)c->n_blocks * kEdgesPerBlock * c->cap;
+    const size_t C = (size_t)c->G * c->H * c->W;
+    const size_t sb = c->sum_bits / 8;
+    CUDA_TRY(e, dalloc(c, &c->perm, E));
+    CUDA_TRY(e, dalloc(c, &c->group, E));
+    CUDA_TRY(e, dalloc(c, &c->weight, E));
+    for (int b = 0; b < 2; ++b) {
+        CUDA_TRY(e, dalloc(c, &c->cnt[b], E));
+        CUDA_TRY(e, dalloc(c, &c->pts[b], region));
+    }
+    CUDA_TRY(e, dalloc(c, &c->hist, C));
+    CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->Y), C * sb));
+    CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->S), C * sb));
+    CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->rho), C * rho_bytes(c->p.rho_dtype)));
+    CUDA_TRY(e, dalloc(c, &c->counters, 4));
+    CUDA_TRY(e, dalloc(c, &c->fetch_off, (size_t)E + 1));
+    CUDA_TRY(e, dalloc(c, &c->fetch_tmp, scan_offsets_tmp_elems(E) + 1));
+    CUDA_TRY(e, cudaMemsetAsync(c->hist, 0, C * sizeof(uint32_t), c->stream));
+    CUDA_TRY(e, cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream));
+    return BUNDLE_OK;
+}
+
+// Spatial sort of the edges into slots: key = (group, Morton tile of the
+// midpoint); a counting sort on the device. The bundling result does not depend
+// on the slot order (every step is per edge, per point or an integer sum).
+bundle_status sort_edges(bundle_ctx* c, const float2* d_src, const float2* d_dst,
+                         const int32_t* d_group_in, const int32_t* d_weight_in, std::string* e) {
+    const int64_t E = c->E;
+    const int32_t nbk = c->G * 4096;
+    uint32_t *key = nullptr, *bucket = nullptr;
+    CUDA_TRY(e, cudaMalloc(&key, (size_t)E * sizeof(uint32_t)));
+    cudaError_t err = cudaMalloc(&bucket, (size_t)nbk * sizeof(uint32_t));
+    if (err != cudaSuccess) {
+        cudaFree(key);
+        CUDA_TRY(e, err);
+    }
+    int32_t* zero_group = nullptr;
+    if (!d_group_in) {
+        err = cudaMalloc(&zero_group, (size_t)E * sizeof(int32_t));
+        if (err == cudaSuccess) err = cudaMemsetAsync(zero_group, 0, (size_t)E * 4, c->stream);
+    }
+    if (err == cudaSuccess) err = cudaMemsetAsync(bucket, 0, (size_t)nbk * 4, c->stream);
+    const int32_t* gsrc = d_group_in ? d_group_in : zero_group;
+    if (err == cudaSuccess)
+        err = launch_edge_keys(d_src, d_dst, gsrc, E, c->W, c->H, key, bucket, c->stream);
+    if (err == cudaSuccess) err = launch_bucket_scan(bucket, nbk, c->stream);
+    if (err == cudaSuccess) err = launch_edge_scatter(key, E, bucket, c->perm, c->stream);
+    if (err == cudaSuccess)
+        err = launch_gather_edges(c->perm, E, gsrc, d_weight_in, c->group, c->weight, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    cudaFree(key);
+    cudaFree(bucket);
+    if (zero_group) cudaFree(zero_group);
+    CUDA_TRY(e, err);
+    return BUNDLE_OK;
+}
+
+bundle_status make_ctx(bundle_ctx** out, const bundle_params* p, int64_t n_edges,
+                       int32_t n_groups, void* stream, bundle_ctx** made, std::string* e) {
+    if (!out) return fail(e, BUNDLE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(e, BUNDLE_EINVAL, "params is NULL");
+    if (n_edges <= 0 || n_edges >= (int64_t)INT32_MAX)
+        return fail(e, BUNDLE_EINVAL, "n_edges must be in [1, 2^31 - 1)");
+    bundle_status s = check_params(*p, n_groups, e);
+    if (s != BUNDLE_OK) return s;
+    bundle_ctx* c = new (std::nothrow) bundle_ctx();
+    if (!c) return fail(e, BUNDLE_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->E = n_edges;
+    c->G = n_groups;
+    c->cap = p->n_fixed > 0 ? p->n_fixed : p->n_max;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->device = -1;
+    *made = c;
+    return BUNDLE_OK;
+}
+
+// Bind the context to the current device and its stream (the first CUDA call
+// of an init; host-side checks run before it).
+bundle_status attach_cuda(bundle_ctx* c, std::string* e) {
+    if (c->device >= 0) return BUNDLE_OK;
+    cudaError_t err = cudaGetDevice(&c->device);
+    if (err != cudaSuccess) {
+        c->device = -1;
+        return fail(e, BUNDLE_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(err));
+    }
+    if (!c->stream) {
+        err = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (err != cudaSuccess) {
+            c->stream = nullptr;
+            return fail(e, BUNDLE_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(err));
+        }
+        c->own_stream = true;
+    }
+    return BUNDLE_OK;
+}
+
+template <typename T>
+bool to_host(const T* p, int64_t n, bool on_device, std::vector<T>* v, const T** view) {
+    if (!p) {
+        *view = nullptr;
+        return true;
+    }
+    if (!on_device) {
+        *view = p;
+        return true;
+    }
+    v->resize((size_t)n);
+    if (cudaMemcpy(v->data(), p, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return false;
+    *view = v->data();
+    return true;
+}
+
+enum ProfileKind { kProfResample = 0, kProfAdvect, kProfAdvectResample, kProfRowbox,
+                   kProfColbox, kProfCombine, kProfHistClear, kProfKinds };
+
+// Launch through `fn`, bracketed by two events when profiling is on.
+template <typename F>
+cudaError_t timed(bundle_ctx* c, int kind, F fn) {
+    if (!c->prof) return fn();
+    while (c->ev_pool.size() < c->ev_used + 2) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        c->ev_pool.push_back(ev);
+    }
+    cudaEvent_t a = c->ev_pool[c->ev_used], b = c->ev_pool[c->ev_used + 1];
+    cudaError_t e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e == cudaSuccess) {
+        c->ev_used += 2;
+        c->ev_kind.push_back(kind);
+    }
+    return e;
+}
+
+bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
+    StepArgs a{};
+    a.cnt_in = c->cnt[in];
+    a.pts_in = c->pts[in];
+    a.cnt_out = c->cnt[out];
+    a.pts_out = c->pts[out];
+    a.group = c->group;
+    a.weight = c->weight;
+    a.rho = c->rho;
+    a.hist = c->hist;
+    a.n_splat = c->counters;
+    a.E = c->E;
+    a.cap = c->cap;
+    a.W = c->W;
+    a.H = c->H;
+    a.h = h;
+    a.eps = c->p.eps;
+    a.tries = c->p.step_tries;
+    a.lap_keep = (float)(1.0 - (double)c->p.laplace_beta);
+    a.lap_half_beta = (float)(0.5 * (double)c->p.laplace_beta);
+    a.n_fixed = c->p.n_fixed;
+    a.n_max = c->p.n_max;
+    a.delta = c->p.delta_px;
+    if (mode & kModeResample)
+        CUDA_TRY(&c->err, timed(c, kProfHistClear, [&] {
+                     return cudaMemsetAsync(c->hist, 0,
+                                            (size_t)c->G * c->H * c->W * sizeof(uint32_t),
+                                            c->stream);
+                 }));
+    const int kind = mode == kModeResample ? kProfResample
+                     : mode == kModeAdvect ? kProfAdvect : kProfAdvectResample;
+    CUDA_TRY(&c->err, timed(c, kind, [&] { return launch_step(mode, c->p.rho_dtype, a, c->stream); }));
+    return BUNDLE_OK;
+}
+
+bundle_status run_filter(bundle_ctx* c) {
+    FilterArgs f{};
+    f.hist = c->hist;
+    f.Y = c->Y;
+    f.S = c->S;
+    f.rho = c->rho;
+    f.G = c->G;
+    f.H = c->H;
+    f.W = c->W;
+    f.r = c->p.radius;
+    f.passes = c->p.passes;
+    f.mix_self = c->mix_self;
+    f.mix_all = c->mix_all;
+    f.den_f = c->den_f;
+    CUDA_TRY(&c->err, timed(c, kProfRowbox, [&] { return launch_rowbox(c->sum_bits, f, c->stream); }));
+    CUDA_TRY(&c->err, timed(c, kProfColbox, [&] { return launch_colbox(c->sum_bits, f, c->stream); }));
+    CUDA_TRY(&c->err, timed(c, kProfCombine, [&] {
+                 return launch_combine(c->sum_bits, c->p.rho_dtype, f, c->stream);
+             }));
+    return BUNDLE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bundle_default_params(bundle_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->grid_w = 0;
+    p->grid_h = 0;
+    p->grid_dominant = 800;
+    p->margin_px = -1;
+    p->radius = 4;
+    p->passes = 3;
+    p->alpha_num = 1;
+    p->alpha_den = 4;
+    p->h_max_sigmas = 2.0;
+    p->lambda = 0.9;
+    p->n_fixed = 0;
+    p->n_max = 64;
+    p->delta_px = 2.0f;
+    p->laplace_beta = 0.5f;
+    p->eps = 1e-9f;
+    p->step_tries = 8;
+    p->sum_bits = 0;
+    p->rho_dtype = BUNDLE_RHO_F32;
+    p->flags = 0;
+}
+
+bundle_status bundle_init(bundle_ctx** out, const bundle_params* p, int64_t n_edges,
+                          const float* src_xy, const float* dst_xy, const int32_t* group,
+                          int32_t n_groups, const int32_t* weight, int32_t flags, void* stream) {
+    std::string* e = &g_init_error;
+    bundle_ctx* c = nullptr;
+    bundle_status s = make_ctx(out, p, n_edges, n_groups, stream, &c, e);
+    if (s != BUNDLE_OK) return s;
+    auto bail = [&](bundle_status st) {
+        free_ctx(c);
+        return st;
+    };
+    if (!src_xy || !dst_xy) return bail(fail(e, BUNDLE_EINVAL, "src_xy and dst_xy are required"));
+    const bool dev = (flags & BUNDLE_INPUT_DEVICE) != 0;
+    if (dev && (s = attach_cuda(c, e)) != BUNDLE_OK) return bail(s);
+    std::vector<float> hs, hd;
+    std::vector<int32_t> hg, hw;
+    const float *vs, *vd;
+    const int32_t *vg, *vw;
+    if (!to_host(src_xy, 2 * n_edges, dev, &hs, &vs) || !to_host(dst_xy, 2 * n_edges, dev, &hd, &vd) ||
+        !to_host(group, n_edges, dev, &hg, &vg) || !to_host(weight, n_edges, dev, &hw, &vw))
+        return bail(fail(e, BUNDLE_ECUDA, "copy of device inputs failed"));
+    if (vg)
+        for (int64_t i = 0; i < n_edges; ++i)
+            if (vg[i] < 0 || vg[i] >= n_groups)
+                return bail(fail(e, BUNDLE_EINVAL, "group[%lld] = %d outside [0, %d)",
+                                 (long long)i, vg[i], n_groups));
+    s = size_integers(c, vw, e);
+    if (s != BUNDLE_OK) return bail(s);
+    std::vector<float> spx, dpx;
+    s = grid_map(c, vs, vd, e, &spx, &dpx);
+    if (s != BUNDLE_OK) return bail(s);
+    if (c->p.radius >= std::min(c->W, c->H))
+        return bail(fail(e, BUNDLE_EINVAL, "radius %d must be below min(W, H) = %d", c->p.radius,
+                         std::min(c->W, c->H)));
+    if ((s = attach_cuda(c, e)) != BUNDLE_OK) return bail(s);
+    DeviceGuard dg(c->device);
+    s = alloc_state(c, e);
+    if (s != BUNDLE_OK) return bail(s);
+    // staging copies of the mapped endpoints, groups and weights
+    float2 *d_src = nullptr, *d_dst = nullptr;
+    int32_t *d_g = nullptr, *d_w = nullptr;
+    cudaError_t err = cudaMalloc(&d_src, (size_t)n_edges * sizeof(float2));
+    if (err == cudaSuccess) err = cudaMalloc(&d_dst, (size_t)n_edges * sizeof(float2));
+    if (err == cudaSuccess && vg) err = cudaMalloc(&d_g, (size_t)n_edges * 4);
+    if (err == cudaSuccess && vw) err = cudaMalloc(&d_w, (size_t)n_edges * 4);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_src, spx.data(), (size_t)n_edges * 8, cudaMemcpyHostToDevice,
+                              c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_dst, dpx.data(), (size_t)n_edges * 8, cudaMemcpyHostToDevice,
+                              c->stream);
+    if (err == cudaSuccess && vg)
+        err = cudaMemcpyAsync(d_g, vg, (size_t)n_edges * 4, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess && vw)
+        err = cudaMemcpyAsync(d_w, vw, (size_t)n_edges * 4, cudaMemcpyHostToDevice, c->stream);
+    bundle_status st = BUNDLE_OK;
+    if (err == cudaSuccess) st = sort_edges(c, d_src, d_dst, d_g, d_w, e);
+    if (err == cudaSuccess && st == BUNDLE_OK)
+        err = launch_straight_layout(c->perm, n_edges, d_src, d_dst, c->cap, c->cnt[0],
+                                     c->pts[0], c->stream);
+    if (err == cudaSuccess && st == BUNDLE_OK) err = cudaStreamSynchronize(c->stream);
+    cudaFree(d_src);
+    cudaFree(d_dst);
+    if (d_g) cudaFree(d_g);
+    if (d_w) cudaFree(d_w);
+    if (st != BUNDLE_OK) return bail(st);
+    if (err != cudaSuccess)
+        return bail(fail(e, err == cudaErrorMemoryAllocation ? BUNDLE_ENOMEM : BUNDLE_ECUDA,
+                         "init staging: %s", cudaGetErrorString(err)));
+    c->cur_P = 0;
+    c->cur_R = -1;
+    *out = c;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_init_polylines(bundle_ctx** out, const bundle_params* p, int64_t n_edges,
+                                    const int64_t* off, const float* xy_px, const int32_t* group,
+                                    int32_t n_groups, const int32_t* weight, const double* map5,
+                                    int32_t iteration, int32_t flags, void* stream) {
+    std::string* e = &g_init_error;
+    bundle_ctx* c = nullptr;
+    bundle_status s = make_ctx(out, p, n_edges, n_groups, stream, &c, e);
+    if (s != BUNDLE_OK) return s;
+    auto bail = [&](bundle_status st) {
+        free_ctx(c);
+        return st;
+    };
+    if (!off || !xy_px) return bail(fail(e, BUNDLE_EINVAL, "off and xy_px are required"));
+    if (p->grid_w < 2 || p->grid_h < 2 || p->grid_w > 4096 || p->grid_h > 4096)
+        return bail(fail(e, BUNDLE_EINVAL, "grid_w and grid_h must be in [2, 4096]"));
+    if (iteration < 0) return bail(fail(e, BUNDLE_EINVAL, "iteration must be >= 0"));
+    c->W = p->grid_w;
+    c->H = p->grid_h;
+    if (c->p.radius >= std::min(c->W, c->H))
+        return bail(fail(e, BUNDLE_EINVAL, "radius must be below min(W, H)"));
+    const bool dev = (flags & BUNDLE_INPUT_DEVICE) != 0;
+    if (dev && (s = attach_cuda(c, e)) != BUNDLE_OK) return bail(s);
+    std::vector<int64_t> ho;
+    std::vector<int32_t> hg, hw;
+    std::vector<float> hx;
+    const int64_t* vo;
+    const int32_t *vg, *vw;
+    const float* vx;
+    if (!to_host(off, n_edges + 1, dev, &ho, &vo))
+        return bail(fail(e, BUNDLE_ECUDA, "copy of device offsets failed"));
+    const int64_t N = vo[n_edges];
+    if (vo[0] != 0 || N <= 0) return bail(fail(e, BUNDLE_EINVAL, "off must start at 0"));
+    for (int64_t i = 0; i < n_edges; ++i) {
+        int64_t n = vo[i + 1] - vo[i];
+        if (n < 2 || n > c->cap)
+            return bail(fail(e, BUNDLE_EINVAL, "polyline %lld has %lld points, need 2..%d",
+                             (long long)i, (long long)n, c->cap));
+    }
+    if (!to_host(xy_px, 2 * N, dev, &hx, &vx) || !to_host(group, n_edges, dev, &hg, &vg) ||
+        !to_host(weight, n_edges, dev, &hw, &vw))
+        return bail(fail(e, BUNDLE_ECUDA, "copy of device inputs failed"));
+    const float hxm = (float)c->W - kEdgeGuard, hym = (float)c->H - kEdgeGuard;
+    for (int64_t k = 0; k < N; ++k)
+        if (!(vx[2 * k] >= 0 && vx[2 * k] <= hxm && vx[2 * k + 1] >= 0 && vx[2 * k + 1] <= hym))
+            return bail(fail(e, BUNDLE_EINVAL, "point %lld lies outside [0, W - 2^-10] x "
+                             "[0, H - 2^-10]", (long long)k));
+    if (vg)
+        for (int64_t i = 0; i < n_edges; ++i)
+            if (vg[i] < 0 || vg[i] >= n_groups)
+                return bail(fail(e, BUNDLE_EINVAL, "group[%lld] outside [0, %d)", (long long)i,
+                                 n_groups));
+    s = size_integers(c, vw, e);
+    if (s != BUNDLE_OK) return bail(s);
+    if (map5) std::memcpy(c->map, map5, sizeof c->map);
+    c->iteration = iteration;
+    if ((s = attach_cuda(c, e)) != BUNDLE_OK) return bail(s);
+    DeviceGuard dg(c->device);
+    s = alloc_state(c, e);
+    if (s != BUNDLE_OK) return bail(s);
+    // midpoint keys from each polyline's endpoints
+    std::vector<float> ends_s((size_t)(2 * n_edges)), ends_d((size_t)(2 * n_edges));
+    for (int64_t i = 0; i < n_edges; ++i) {
+        ends_s[2 * i] = vx[2 * vo[i]];
+        ends_s[2 * i + 1] = vx[2 * vo[i] + 1];
+        ends_d[2 * i] = vx[2 * (vo[i + 1] - 1)];
+        ends_d[2 * i + 1] = vx[2 * (vo[i + 1] - 1) + 1];
+    }
+    float2 *d_src = nullptr, *d_dst = nullptr, *d_xy = nullptr;
+    int32_t *d_g = nullptr, *d_w = nullptr;
+    int64_t* d_off = nullptr;
+    cudaError_t err = cudaMalloc(&d_src, (size_t)n_edges * 8);
+    if (err == cudaSuccess) err = cudaMalloc(&d_dst, (size_t)n_edges * 8);
+    if (err == cudaSuccess) err = cudaMalloc(&d_xy, (size_t)N * 8);
+    if (err == cudaSuccess) err = cudaMalloc(&d_off, (size_t)(n_edges + 1) * 8);
+    if (err == cudaSuccess && vg) err = cudaMalloc(&d_g, (size_t)n_edges * 4);
+    if (err == cudaSuccess && vw) err = cudaMalloc(&d_w, (size_t)n_edges * 4);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(d_src, ends_s.data(), (size_t)n_edges * 8, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(d_dst, ends_d.data(), (size_t)n_edges * 8, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(d_xy, vx, (size_t)N * 8, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(d_off, vo, (size_t)(n_edges + 1) * 8, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && vg)
+        err = cudaMemcpy(d_g, vg, (size_t)n_edges * 4, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && vw)
+        err = cudaMemcpy(d_w, vw, (size_t)n_edges * 4, cudaMemcpyHostToDevice);
+    bundle_status st = BUNDLE_OK;
+    if (err == cudaSuccess) st = sort_edges(c, d_src, d_dst, d_g, d_w, e);
+    if (err == cudaSuccess && st == BUNDLE_OK)
+        err = launch_polyline_layout(c->perm, n_edges, d_off, d_xy, c->cap, c->cnt[0], c->pts[0],
+                                     c->stream);
+    if (err == cudaSuccess && st == BUNDLE_OK) err = cudaStreamSynchronize(c->stream);
+    cudaFree(d_src);
+    cudaFree(d_dst);
+    cudaFree(d_xy);
+    cudaFree(d_off);
+    if (d_g) cudaFree(d_g);
+    if (d_w) cudaFree(d_w);
+    if (st != BUNDLE_OK) return bail(st);
+    if (err != cudaSuccess)
+        return bail(fail(e, err == cudaErrorMemoryAllocation ? BUNDLE_ENOMEM : BUNDLE_ECUDA,
+                         "init staging: %s", cudaGetErrorString(err)));
+    c->cur_P = 0;
+    c->cur_R = -1;
+    *out = c;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
+    if (!c) return BUNDLE_EINVAL;
+    if (n_iters < 0) return fail(&c->err, BUNDLE_EINVAL, "n_iters must be >= 0");
+    if (n_iters == 0) return BUNDLE_OK;
+    DeviceGuard dg(c->device);
+    // resample the current polylines and splat them (start of the first iteration)
+    int src = c->cur_P, dst = 1 - c->cur_P;
+    bundle_status s = run_step(c, kModeResample, src, dst, 0.0f);
+    if (s != BUNDLE_OK) return s;
+    int R = dst;
+    for (int32_t it = 0; it < n_iters; ++it) {
+        s = run_filter(c);
+        if (s != BUNDLE_OK) return s;
+        float h = (float)bandwidth(c->p, c->iteration);
+        bool last = it == n_iters - 1;
+        s = run_step(c, last ? kModeAdvect : kModeAdvectResample, R, 1 - R, h);
+        if (s != BUNDLE_OK) return s;
+        c->iteration += 1;
+        if (last) {
+            c->cur_P = 1 - R;
+            c->cur_R = R;
+        } else {
+            R = 1 - R;
+        }
+    }
+    c->have_density = true;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_sync(bundle_ctx* c) {
+    if (!c) return BUNDLE_EINVAL;
+    DeviceGuard dg(c->device);
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(&c->err, cudaGetLastError());
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_fetch(bundle_ctx* c, int64_t* off, float* xy, int64_t cap,
+                           int64_t* n_points, int32_t flags) {
+    if (!c) return BUNDLE_EINVAL;
+    if (!off || !n_points) return fail(&c->err, BUNDLE_EINVAL, "off and n_points are required");
+    int sel = c->cur_P;
+    if (flags & BUNDLE_FETCH_RESAMPLED) {
+        if (c->cur_R < 0)
+            return fail(&c->err, BUNDLE_ESTATE, "no iteration has run: nothing was resampled");
+        sel = c->cur_R;
+    }
+    DeviceGuard dg(c->device);
+    const bool dev = (flags & BUNDLE_FETCH_DEVICE) != 0;
+    const bool pix = (flags & BUNDLE_FETCH_PIXELS) != 0;
+    CUDA_TRY(&c->err, launch_counts_to_caller(c->perm, c->cnt[sel], c->E, c->fetch_off, c->stream));
+    CUDA_TRY(&c->err, launch_scan_offsets(c->fetch_off, c->E, c->fetch_tmp, c->stream));
+    int64_t N = 0;
+    CUDA_TRY(&c->err, cudaMemcpyAsync(&N, c->fetch_off + c->E, sizeof N, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    *n_points = N;
+    if (dev) {
+        CUDA_TRY(&c->err, cudaMemcpyAsync(off, c->fetch_off, (size_t)(c->E + 1) * 8,
+                                          cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CUDA_TRY(&c->err, cudaMemcpyAsync(off, c->fetch_off, (size_t)(c->E + 1) * 8,
+                                          cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (xy) {
+        if (cap < N) {
+            cudaStreamSynchronize(c->stream);
+            return fail(&c->err, BUNDLE_EINVAL, "xy holds %lld points, %lld needed",
+                        (long long)cap, (long long)N);
+        }
+        float2* target = reinterpret_cast<float2*>(xy);
+        if (!dev) {
+            if (c->fetch_xy_cap < N) {
+                if (c->fetch_xy) {
+                    cudaFree(c->fetch_xy);
+                    c->device_bytes -= c->fetch_xy_cap * 8;
+                }
+                c->fetch_xy = nullptr;
+                c->fetch_xy_cap = 0;
+                CUDA_TRY(&c->err, dalloc(c, &c->fetch_xy, (size_t)N));
+                c->fetch_xy_cap = N;
+            }
+            target = c->fetch_xy;
+        }
+        const double inv = 1.0 / c->map[2];
+        CUDA_TRY(&c->err, launch_layout_to_caller(c->perm, c->cnt[sel], c->pts[sel], c->E, c->cap,
+                                                  c->fetch_off, target, pix ? 0 : 1,
+                                                  (float)c->map[3], (float)c->map[4], (float)inv,
+                                                  (float)c->map[0], (float)c->map[1], c->stream));
+        if (!dev)
+            CUDA_TRY(&c->err, cudaMemcpyAsync(xy, target, (size_t)N * 8, cudaMemcpyDeviceToHost,
+                                              c->stream));
+    }
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int64_t dst_bytes,
+                                   int32_t flags) {
+    if (!c) return BUNDLE_EINVAL;
+    if (!dst) return fail(&c->err, BUNDLE_EINVAL, "dst is NULL");
+    if (!c->have_density) return fail(&c->err, BUNDLE_ESTATE, "no iteration has run");
+    const size_t C = (size_t)c->G * c->H * c->W;
+    const void* src;
+    size_t bytes;
+    switch (which) {
+        case BUNDLE_DENSITY_HIST: src = c->hist; bytes = C * 4; break;
+        case BUNDLE_DENSITY_SUMS: src = c->S; bytes = C * (c->sum_bits / 8); break;
+        case BUNDLE_DENSITY_RHO: src = c->rho; bytes = C * rho_bytes(c->p.rho_dtype); break;
+        default: return fail(&c->err, BUNDLE_EINVAL, "unknown density selector %d", which);
+    }
+    if (dst_bytes < (int64_t)bytes)
+        return fail(&c->err, BUNDLE_EINVAL, "dst holds %lld bytes, %zu needed",
+                    (long long)dst_bytes, bytes);
+    DeviceGuard dg(c->device);
+    CUDA_TRY(&c->err, cudaMemcpyAsync(dst, src, bytes,
+                                      (flags & BUNDLE_FETCH_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                    : cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_get_info(const bundle_ctx* c, bundle_info* out) {
+    if (!c || !out) return BUNDLE_EINVAL;
+    bundle_ctx* m = const_cast<bundle_ctx*>(c);
+    DeviceGuard dg(c->device);
+    std::memset(out, 0, sizeof *out);
+    out->n_edges = c->E;
+    out->grid_w = c->W;
+    out->grid_h = c->H;
+    out->n_groups = c->G;
+    out->sum_bits = c->sum_bits;
+    out->rho_dtype = c->p.rho_dtype;
+    out->iteration = c->iteration;
+    std::memcpy(out->map, c->map, sizeof c->map);
+    out->h_next = bandwidth(c->p, c->iteration);
+    out->device_bytes = c->device_bytes;
+    unsigned long long tot[2] = {0, 0};
+    int sels[2] = {c->cur_P, c->cur_R};
+    for (int k = 0; k < 2; ++k) {
+        if (sels[k] < 0) continue;
+        if (cudaMemsetAsync(m->counters + 1, 0, 8, c->stream) != cudaSuccess) return BUNDLE_ECUDA;
+        if (launch_sum_counts(c->cnt[sels[k]], c->E, m->counters + 1, c->stream) != cudaSuccess)
+            return BUNDLE_ECUDA;
+        if (cudaMemcpyAsync(&tot[k], m->counters + 1, 8, cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return BUNDLE_ECUDA;
+    }
+    out->n_points = (int64_t)tot[0];
+    out->n_points_resampled = (int64_t)tot[1];
+    unsigned long long done = 0;
+    if (cudaMemcpyAsync(&done, m->counters, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return BUNDLE_ECUDA;
+    out->points_processed = (int64_t)done;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_profile_enable(bundle_ctx* c, int32_t on) {
+    if (!c) return BUNDLE_EINVAL;
+    c->prof = on != 0;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_profile_read(bundle_ctx* c, double* ms, int64_t* launches, int32_t n,
+                                  int32_t reset) {
+    if (!c) return BUNDLE_EINVAL;
+    if (n < 0 || (n > 0 && (!ms || !launches)))
+        return fail(&c->err, BUNDLE_EINVAL, "ms and launches must hold n entries");
+    DeviceGuard dg(c->device);
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    for (int32_t k = 0; k < n; ++k) {
+        ms[k] = 0;
+        launches[k] = 0;
+    }
+    for (size_t r = 0; r < c->ev_kind.size(); ++r) {
+        float t = 0;
+        CUDA_TRY(&c->err, cudaEventElapsedTime(&t, c->ev_pool[2 * r], c->ev_pool[2 * r + 1]));
+        int k = c->ev_kind[r];
+        if (k < n) {
+            ms[k] += t;
+            launches[k] += 1;
+        }
+    }
+    if (reset) {
+        c->ev_kind.clear();
+        c->ev_used = 0;
+    }
+    return BUNDLE_OK;
+}
+
+void bundle_destroy(bundle_ctx* c) { free_ctx(c); }
+
+const char* bundle_last_error(const bundle_ctx* c) {
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+const char* bundle_status_string(bundle_status s) {
+    switch (s) {
+        case BUNDLE_OK: return "BUNDLE_OK";
+        case BUNDLE_EINVAL: return "BUNDLE_EINVAL";
+        case BUNDLE_ENOMEM: return "BUNDLE_ENOMEM";
+        case BUNDLE_ECUDA: return "BUNDLE_ECUDA";
+        case BUNDLE_EOVERFLOW: return "BUNDLE_EOVERFLOW";
+        case BUNDLE_ETIMEOUT: return "BUNDLE_ETIMEOUT";
+        case BUNDLE_ESTATE: return "BUNDLE_ESTATE";
+        case BUNDLE_ENOTSUP: return "BUNDLE_ENOTSUP";
+    }
+    return "BUNDLE_UNKNOWN";
+}
+
+}  // extern "C"

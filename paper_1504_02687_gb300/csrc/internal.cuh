@@ -1,0 +1,96 @@
+// Internal declarations shared by the kernel translation units and the host
+// side of the bundling library. Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace heb {
+
+// Point layout. Edges live in blocks of kEdgesPerBlock consecutive (spatially
+// sorted) slots; block b owns the point region [b * kEdgesPerBlock * cap,
+// (b+1) * kEdgesPerBlock * cap) of a float2 buffer, and packs its edges'
+// polylines back to back inside it, in slot order. Only the per-slot point
+// counts are stored: a block recovers its edges' offsets with one scan.
+constexpr int kEdgesPerBlock = 128;
+constexpr int kStepThreads = 256;
+constexpr int kBatchPoints = 2048;  // points staged in shared memory per batch
+constexpr int kMaxCap = 256;        // largest polyline (n_fixed or n_max)
+constexpr float kEdgeGuard = 0.0009765625f;  // positions stay below W - 2^-10
+
+enum StepMode : int {
+    kModeResample = 2,                // resample + splat the input polylines
+    kModeAdvect = 1,                  // advect + Laplacian, write polylines
+    kModeAdvectResample = 3,          // advect + Laplacian + resample + splat
+};
+
+struct StepArgs {
+    const int32_t* cnt_in;   // [E] points per slot (input layout)
+    const float2* pts_in;    // input polylines (block layout)
+    int32_t* cnt_out;        // [E] points per slot (output layout)
+    float2* pts_out;         // output polylines (block layout)
+    const int32_t* group;    // [E] per slot
+    const int32_t* weight;   // [E] per slot
+    const void* rho;         // [G][H][W] density, element type per rho_dtype
+    uint32_t* hist;          // [G][H][W] histogram accumulated by the splat
+    unsigned long long* n_splat;  // running count of splatted points
+    int64_t E;
+    int32_t cap;             // points per slot of the region (n_fixed or n_max)
+    int32_t W, H;
+    float h;                 // step magnitude h_i
+    float eps;               // Eq. 5 epsilon
+    int32_t tries;           // step sizes tried
+    float lap_keep;          // 1 - beta
+    float lap_half_beta;     // beta / 2
+    int32_t n_fixed, n_max;
+    float delta;
+};
+
+struct FilterArgs {
+    const uint32_t* hist;  // [G][H][W]
+    void* Y;               // [G][H][W] row-filtered workspace (sum type)
+    void* S;               // [G][H][W] smoothed sums (sum type)
+    void* rho;             // [G][H][W] density (rho type)
+    int32_t G, H, W, r, passes;
+    int64_t mix_self;      // q (G - 1) + p : weight of a group's own layer
+    int64_t mix_all;       // p : weight of the all-groups sum
+    float inv_den_f;       // unused (kept for a future reciprocal form)
+    float den_f;           // q (G - 1) s^k (or s^k for one group), rounded to float
+};
+
+// Launchers (return the launch status; nothing here synchronises).
+cudaError_t launch_step(int mode, int rho_dtype, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st);
+
+// Init / fetch helpers (point layout <-> caller order).
+cudaError_t launch_edge_keys(const float2* src, const float2* dst, const int32_t* group,
+                             int64_t E, int32_t W, int32_t H, uint32_t* key, uint32_t* bucket_cnt,
+                             cudaStream_t st);
+cudaError_t launch_bucket_scan(uint32_t* cnt, int32_t n_buckets, cudaStream_t st);
+cudaError_t launch_edge_scatter(const uint32_t* key, int64_t E, uint32_t* cursor, int32_t* perm,
+                                cudaStream_t st);
+cudaError_t launch_gather_edges(const int32_t* perm, int64_t E, const int32_t* group_in,
+                                const int32_t* weight_in, int32_t* group_out,
+                                int32_t* weight_out, cudaStream_t st);
+cudaError_t launch_straight_layout(const int32_t* perm, int64_t E, const float2* src,
+                                   const float2* dst, int32_t cap, int32_t* cnt, float2* pts,
+                                   cudaStream_t st);
+cudaError_t launch_polyline_layout(const int32_t* perm, int64_t E, const int64_t* off,
+                                   const float2* xy, int32_t cap, int32_t* cnt, float2* pts,
+                                   cudaStream_t st);
+cudaError_t launch_counts_to_caller(const int32_t* perm, const int32_t* cnt, int64_t E,
+                                    int64_t* off_out, cudaStream_t st);
+cudaError_t launch_scan_offsets(int64_t* off, int64_t E, int64_t* tmp, cudaStream_t st);
+cudaError_t launch_layout_to_caller(const int32_t* perm, const int32_t* cnt, const float2* pts,
+                                    int64_t E, int32_t cap, const int64_t* off, float2* xy_out,
+                                    int32_t to_world, float ox, float oy, float inv_scale,
+                                    float xmin, float ymin, cudaStream_t st);
+cudaError_t launch_sum_counts(const int32_t* cnt, int64_t E, unsigned long long* total,
+                              cudaStream_t st);
+size_t scan_offsets_tmp_elems(int64_t E);
+
+}  // namespace heb

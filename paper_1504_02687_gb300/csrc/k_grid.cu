@@ -1,0 +1,228 @@
+// Grid-side kernels of the bundling iteration: the repeated box filters of
+// Sec. 3.1 and the layer interaction of Eq. 3 / Eq. 4.
+//
+// A (2r+1) x (2r+1) box sum is separable: it equals a (2r+1)-wide running sum
+// along every row followed by one along every column, and with per-axis
+// half-sample reflection the row and column passes commute. k passes of the 2D
+// box therefore equal k row passes followed by k column passes, computed here
+// by two kernels that each keep a whole row (or a strip of columns) in shared
+// memory. Each 1D pass is the difference form of a 1D integral image kept as a
+// running window sum. All sums are unsigned integers: modular wrap-around
+// cancels exactly, so every box sum that fits its type is exact.
+#include "internal.cuh"
+
+namespace heb {
+namespace {
+
+__device__ __forceinline__ int reflect_index(int i, int n) {
+    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+}
+
+// ------------------------------------------------------------------ row passes
+// One warp per row, `rows` warps per CTA. Lane l owns the contiguous chunk
+// [l*c, (l+1)*c) of the row; the shared row is padded after every chunk so the
+// 32 lanes walking their chunks in lockstep hit distinct banks.
+template <typename TS>
+__global__ void k_rowbox(const uint32_t* __restrict__ hist, TS* __restrict__ Y, int G, int H,
+                         int W, int r, int passes, int rows, int c, int pad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.y;
+    const int v = blockIdx.x * rows + warp;
+    if (v >= H) return;
+    const int stride = W + 32 * pad;
+    TS* src = reinterpret_cast<TS*>(smem_raw) + (size_t)warp * 2 * stride;
+    TS* dst = src + stride;
+    const size_t base = ((size_t)g * H + v) * W;
+    for (int x = lane; x < W; x += 32) src[x + (x / c) * pad] = (TS)hist[base + x];
+    __syncwarp();
+    const int i0 = lane * c, i1 = min(i0 + c, W);
+    for (int p = 0; p < passes; ++p) {
+        if (i0 < i1) {
+            TS s = 0;
+            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t) {
+                int q = reflect_index(t, W);
+                s += src[q + (q / c) * pad];
+            }
+            for (int i = i0; i < i1; ++i) {
+                int qa = reflect_index(i + r, W), qs = reflect_index(i - r - 1, W);
+                s += src[qa + (qa / c) * pad] - src[qs + (qs / c) * pad];
+                dst[i + (i / c) * pad] = s;
+            }
+        }
+        __syncwarp();
+        TS* t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int x = lane; x < W; x += 32) Y[base + x] = src[x + (x / c) * pad];
+}
+
+// --------------------------------------------------------------- column passes
+// One CTA per strip of STRIP columns of one layer, the whole column height in
+// shared memory. Thread (j, ch) owns column j and the 32-row chunk ch; its 32
+// outputs of a pass stay in registers until the whole CTA has read the pass's
+// input. A pad row after every chunk spreads the chunks over the banks. The
+// strip narrows (8, 4, 2 columns) as the height grows so that a CTA keeps 256
+// threads and the strip fits in shared memory.
+constexpr int kChunk = 32;
+constexpr int kColThreads = 256;
+
+template <typename TS, int STRIP>
+__global__ void __launch_bounds__(kColThreads)
+    k_colbox(const TS* __restrict__ Y, TS* __restrict__ S, int G, int H, int W, int r,
+             int passes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TS* buf = reinterpret_cast<TS*>(smem_raw);
+    const int g = blockIdx.y;
+    const int x0 = blockIdx.x * STRIP;
+    const int j = threadIdx.x % STRIP, ch = threadIdx.x / STRIP;
+    const size_t lay = (size_t)g * H * W;
+    auto prow = [](int row) { return row + row / kChunk; };
+    for (int idx = threadIdx.x; idx < H * STRIP; idx += blockDim.x) {
+        int row = idx / STRIP, col = idx % STRIP, x = x0 + col;
+        buf[prow(row) * STRIP + col] = x < W ? Y[lay + (size_t)row * W + x] : (TS)0;
+    }
+    __syncthreads();
+    const int i0 = ch * kChunk;
+    const int len = max(0, min(kChunk, H - i0));
+    TS out[kChunk];
+    for (int p = 0; p < passes; ++p) {
+        if (len > 0) {
+            TS s = 0;
+            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t)
+                s += buf[prow(reflect_index(t, H)) * STRIP + j];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                if (q < len) {
+                    int i = i0 + q;
+                    s += buf[prow(reflect_index(i + r, H)) * STRIP + j] -
+                         buf[prow(reflect_index(i - r - 1, H)) * STRIP + j];
+                    out[q] = s;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+            if (q < len) buf[prow(i0 + q) * STRIP + j] = out[q];
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < H * STRIP; idx += blockDim.x) {
+        int row = idx / STRIP, col = idx % STRIP, x = x0 + col;
+        if (x < W) S[lay + (size_t)row * W + x] = buf[prow(row) * STRIP + col];
+    }
+}
+
+// -------------------------------------------------------------- layer mixing
+// Eq. 3 / Eq. 4 after smoothing: with alpha = p / q and B groups,
+//   rho_l = (S_l - alpha / (B - 1) * sum_{b != l} S_b) / s^k
+//         = ((q (B-1) + p) S_l - p T) / (q (B-1) s^k),  T = sum_b S_b,
+// whose numerator is an exact int64; one rounding gives the stored density.
+template <typename R>
+__device__ __forceinline__ R to_rho(float v);
+template <>
+__device__ __forceinline__ float to_rho<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_rho<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half to_rho<__half>(float v) { return __float2half_rn(v); }
+
+template <typename TS, typename R>
+__global__ void k_combine(const TS* __restrict__ S, R* __restrict__ rho, int G, int64_t C,
+                          int64_t mix_self, int64_t mix_all, float den) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= C) return;
+    if (G == 1) {
+        long long v = (long long)S[idx];
+        rho[idx] = to_rho<R>(__fdiv_rn(__ll2float_rn(v), den));
+        return;
+    }
+    long long T = 0;
+    for (int g = 0; g < G; ++g) T += (long long)S[(size_t)g * C + idx];
+    for (int g = 0; g < G; ++g) {
+        long long num = mix_self * (long long)S[(size_t)g * C + idx] - mix_all * T;
+        rho[(size_t)g * C + idx] = to_rho<R>(__fdiv_rn(__ll2float_rn(num), den));
+    }
+}
+
+template <typename TS>
+cudaError_t rowbox_t(const FilterArgs& a, cudaStream_t st) {
+    const int c = (a.W + 31) / 32;
+    const int pad = (c % 2 == 0) ? 1 : 2;
+    const size_t per_row = (size_t)2 * (a.W + 32 * pad) * sizeof(TS);
+    size_t fit = (200u * 1024u) / per_row;
+    int rows = (int)(fit < 4 ? fit : 4);
+    if (rows < 1) return cudaErrorInvalidValue;
+    size_t smem = per_row * rows;
+    auto kern = k_rowbox<TS>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)((a.H + rows - 1) / rows), (unsigned)a.G);
+    kern<<<grid, 32 * rows, smem, st>>>(a.hist, static_cast<TS*>(a.Y), a.G, a.H, a.W, a.r,
+                                        a.passes, rows, c, pad);
+    return cudaGetLastError();
+}
+
+template <typename TS, int STRIP>
+cudaError_t colbox_strip(const FilterArgs& a, cudaStream_t st) {
+    const int nch = (a.H + kChunk - 1) / kChunk;
+    if (STRIP * nch > kColThreads) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(a.H + nch) * STRIP * sizeof(TS);
+    auto kern = k_colbox<TS, STRIP>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)((a.W + STRIP - 1) / STRIP), (unsigned)a.G);
+    kern<<<grid, kColThreads, smem, st>>>(static_cast<const TS*>(a.Y), static_cast<TS*>(a.S),
+                                          a.G, a.H, a.W, a.r, a.passes);
+    return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
+    if (a.H <= 1024) return colbox_strip<TS, 8>(a, st);
+    if (a.H <= 2048) return colbox_strip<TS, 4>(a, st);
+    return colbox_strip<TS, 2>(a, st);
+}
+
+template <typename TS, typename R>
+cudaError_t combine_t(const FilterArgs& a, cudaStream_t st) {
+    const int64_t C = (int64_t)a.H * a.W;
+    k_combine<TS, R><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(
+        static_cast<const TS*>(a.S), static_cast<R*>(a.rho), a.G, C, a.mix_self, a.mix_all,
+        a.den_f);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
+    return sum_bits == 32 ? rowbox_t<uint32_t>(a, st) : rowbox_t<unsigned long long>(a, st);
+}
+
+cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
+    return sum_bits == 32 ? colbox_t<uint32_t>(a, st) : colbox_t<unsigned long long>(a, st);
+}
+
+cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st) {
+    if (sum_bits == 32) {
+        switch (rho_dtype) {
+            case 0: return combine_t<uint32_t, float>(a, st);
+            case 1: return combine_t<uint32_t, __nv_bfloat16>(a, st);
+            case 2: return combine_t<uint32_t, __half>(a, st);
+        }
+    } else {
+        switch (rho_dtype) {
+            case 0: return combine_t<unsigned long long, float>(a, st);
+            case 1: return combine_t<unsigned long long, __nv_bfloat16>(a, st);
+            case 2: return combine_t<unsigned long long, __half>(a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace heb

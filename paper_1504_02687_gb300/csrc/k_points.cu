@@ -1,0 +1,624 @@
+// Point-side kernels of the bundling iteration: advection with the halving
+// step and Laplacian smoothing (Eq. 5, Sec. 3.3), resampling (Sec. 2.1,
+// Sec. 3) and the per-group histogram splat (Eq. 1, Eq. 3), fused into one
+// pass over the block layout of the polylines.
+//
+// Every floating-point step is written with explicit round-to-nearest
+// intrinsics so that the fused and the split launch sequences produce the same
+// bits regardless of how the compiler contracts expressions.
+#include "internal.cuh"
+
+namespace heb {
+namespace {
+
+__device__ __forceinline__ int reflect_index(int i, int n) {
+    // half-sample symmetric reflection: -1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2
+    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+}
+
+template <typename T>
+__device__ __forceinline__ float load_rho(const T* p);
+template <>
+__device__ __forceinline__ float load_rho<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_rho<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+template <>
+__device__ __forceinline__ float load_rho<__half>(const __half* p) {
+    return __half2float(__ldg(p));
+}
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float f) {
+    return __fmaf_rn(f, __fsub_rn(b, a), a);
+}
+
+// Bilinear density of one layer at (x, y): cell centres sit at (a + 0.5, b + 0.5).
+template <typename T>
+__device__ __forceinline__ float density_at(const T* __restrict__ L, int W, int H, float x,
+                                            float y) {
+    float u = __fsub_rn(x, 0.5f), v = __fsub_rn(y, 0.5f);
+    float fa = floorf(u), fb = floorf(v);
+    // positions stay in [0, W - 2^-10]; the clamp keeps every index on the map regardless
+    int a0 = min(max((int)fa, -1), W - 1), b0 = min(max((int)fb, -1), H - 1);
+    float fu = __fsub_rn(u, fa), fv = __fsub_rn(v, fb);
+    int c0 = reflect_index(a0, W), c1 = reflect_index(a0 + 1, W);
+    const T* r0 = L + (size_t)reflect_index(b0, H) * W;
+    const T* r1 = L + (size_t)reflect_index(b0 + 1, H) * W;
+    float e00 = load_rho(r0 + c0), e10 = load_rho(r0 + c1);
+    float e01 = load_rho(r1 + c0), e11 = load_rho(r1 + c1);
+    return lerp_rn(lerp_rn(e00, e10, fu), lerp_rn(e01, e11, fu), fv);
+}
+
+__device__ __forceinline__ float clamp_pos(float v, int n) {
+    float hi = __fsub_rn((float)n, kEdgeGuard);
+    return fminf(fmaxf(v, 0.0f), hi);
+}
+
+// Advection of one interior point (Eq. 5) with the optimised step (Sec. 3.3):
+// the direction is the bilinear interpolation of central differences at the
+// four surrounding cell centres on the reflection-extended map; the magnitude
+// starts at h and halves until the density is not lower than at x.
+template <typename T>
+__device__ float2 advect_point(float2 p, const T* __restrict__ L, int W, int H, float h,
+                               float eps, int tries) {
+    float u = __fsub_rn(p.x, 0.5f), v = __fsub_rn(p.y, 0.5f);
+    float fa = floorf(u), fb = floorf(v);
+    int a0 = min(max((int)fa, -1), W - 1), b0 = min(max((int)fb, -1), H - 1);
+    float fu = __fsub_rn(u, fa), fv = __fsub_rn(v, fb);
+    int cm = reflect_index(a0 - 1, W), c0 = reflect_index(a0, W);
+    int c1 = reflect_index(a0 + 1, W), c2 = reflect_index(a0 + 2, W);
+    const T* rm = L + (size_t)reflect_index(b0 - 1, H) * W;
+    const T* r0 = L + (size_t)reflect_index(b0, H) * W;
+    const T* r1 = L + (size_t)reflect_index(b0 + 1, H) * W;
+    const T* r2 = L + (size_t)reflect_index(b0 + 2, H) * W;
+    // 4 x 4 neighbourhood without its corners
+    float e0m = load_rho(rm + c0), e1m = load_rho(rm + c1);
+    float em0 = load_rho(r0 + cm), e00 = load_rho(r0 + c0), e10 = load_rho(r0 + c1),
+          e20 = load_rho(r0 + c2);
+    float em1 = load_rho(r1 + cm), e01 = load_rho(r1 + c0), e11 = load_rho(r1 + c1),
+          e21 = load_rho(r1 + c2);
+    float e02 = load_rho(r2 + c0), e12 = load_rho(r2 + c1);
+    float gx00 = __fmul_rn(__fsub_rn(e10, em0), 0.5f), gx10 = __fmul_rn(__fsub_rn(e20, e00), 0.5f);
+    float gx01 = __fmul_rn(__fsub_rn(e11, em1), 0.5f), gx11 = __fmul_rn(__fsub_rn(e21, e01), 0.5f);
+    float gy00 = __fmul_rn(__fsub_rn(e01, e0m), 0.5f), gy10 = __fmul_rn(__fsub_rn(e11, e1m), 0.5f);
+    float gy01 = __fmul_rn(__fsub_rn(e02, e00), 0.5f), gy11 = __fmul_rn(__fsub_rn(e12, e10), 0.5f);
+    float gx = lerp_rn(lerp_rn(gx00, gx10, fu), lerp_rn(gx01, gx11, fu), fv);
+    float gy = lerp_rn(lerp_rn(gy00, gy10, fu), lerp_rn(gy01, gy11, fu), fv);
+    float rho0 = lerp_rn(lerp_rn(e00, e10, fu), lerp_rn(e01, e11, fu), fv);
+    float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+    float den = fmaxf(nrm, eps);
+    float dx = __fdiv_rn(gx, den), dy = __fdiv_rn(gy, den);
+    float m = h;
+    for (int t = 0; t < tries; ++t) {
+        float xn = clamp_pos(__fmaf_rn(m, dx, p.x), W);
+        float yn = clamp_pos(__fmaf_rn(m, dy, p.y), H);
+        if (density_at(L, W, H, xn, yn) >= rho0) return make_float2(xn, yn);
+        m = __fmul_rn(m, 0.5f);
+    }
+    return p;
+}
+
+__device__ __forceinline__ float seg_len(float2 a, float2 b) {
+    float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y);
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+}
+
+// Point count after resampling (Sec. 2.1: spacing delta; fixed count if set).
+__device__ __forceinline__ int new_count(float L, const StepArgs& a) {
+    if (a.n_fixed > 0) return a.n_fixed;
+    float q = __fdiv_rn(L, a.delta);
+    if (!(q < (float)a.n_max)) return a.n_max;  // also catches NaN
+    int n = (int)ceilf(q) + 1;
+    return n < 2 ? 2 : (n > a.n_max ? a.n_max : n);
+}
+
+// Exclusive scan of in[0..n) into out[0..n] (out[n] = total), n <= blockDim.x.
+__device__ void block_scan_excl(const int* in, int* out, int n, int* warp_tot) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int v = tid < n ? in[tid] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    int base = wid > 0 ? warp_tot[wid - 1] : 0;
+    if (tid < n) out[tid] = base + x - v;
+    if (tid == n - 1) out[n] = base + x;
+    if (n == 0 && tid == 0) out[0] = 0;
+    __syncthreads();
+}
+
+// Largest i in [lo, hi) with arr[i] <= key (arr strictly increasing on [lo, hi)).
+__device__ __forceinline__ int find_slot(const int* arr, int lo, int hi, int key) {
+    hi -= 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (arr[mid] <= key) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
+    __shared__ int s_cnt[kEdgesPerBlock];
+    __shared__ int s_loc[kEdgesPerBlock + 1];
+    __shared__ int s_grp[kEdgesPerBlock];
+    __shared__ int s_w[kEdgesPerBlock];
+    __shared__ int s_nn[kEdgesPerBlock];
+    __shared__ int s_locn[kEdgesPerBlock + 1];
+    __shared__ float s_len[kEdgesPerBlock];
+    __shared__ int s_wtot[32];
+    __shared__ float2 s_pts[kBatchPoints];
+    __shared__ float s_cum[kBatchPoints];
+    constexpr int kPerThread = kBatchPoints / kStepThreads;
+
+    const int tid = threadIdx.x;
+    const int64_t e0 = (int64_t)blockIdx.x * kEdgesPerBlock;
+    const int nb = (int)min((int64_t)kEdgesPerBlock, a.E - e0);
+    const int64_t region = (int64_t)blockIdx.x * kEdgesPerBlock * a.cap;
+    const size_t C = (size_t)a.W * a.H;
+
+    for (int i = tid; i < nb; i += kStepThreads) {
+        s_cnt[i] = a.cnt_in[e0 + i];
+        s_grp[i] = a.group[e0 + i];
+        s_w[i] = a.weight[e0 + i];
+    }
+    __syncthreads();
+    block_scan_excl(s_cnt, s_loc, nb, s_wtot);
+
+    int out_base = 0;
+    for (int b0 = 0; b0 < nb;) {
+        // the longest run of whole polylines that fits the staging buffer
+        int b1;
+        {
+            int lim = s_loc[b0] + kBatchPoints, lo = b0 + 1, hi = nb;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_loc[mid] <= lim) lo = mid; else hi = mid - 1;
+            }
+            b1 = lo;
+        }
+        const int p0 = s_loc[b0];
+        const int np = s_loc[b1] - p0;
+        for (int k = tid; k < np; k += kStepThreads) s_pts[k] = a.pts_in[region + p0 + k];
+        __syncthreads();
+
+        if (MODE & kModeAdvect) {
+            // advection (Eq. 5 + halving step), in place: each point reads only itself
+            for (int k = tid; k < np; k += kStepThreads) {
+                int i = find_slot(s_loc, b0, b1, p0 + k);
+                int j = p0 + k - s_loc[i];
+                if (j > 0 && j < s_cnt[i] - 1) {
+                    const T* L = static_cast<const T*>(a.rho) + (size_t)s_grp[i] * C;
+                    s_pts[k] = advect_point(s_pts[k], L, a.W, a.H, a.h, a.eps, a.tries);
+                }
+            }
+            __syncthreads();
+            // Laplacian smoothing (one Jacobi pass, endpoints fixed)
+            float2 keep[kPerThread];
+#pragma unroll
+            for (int q = 0; q < kPerThread; ++q) {
+                int k = tid + q * kStepThreads;
+                if (k < np) {
+                    int i = find_slot(s_loc, b0, b1, p0 + k);
+                    int j = p0 + k - s_loc[i];
+                    float2 A = s_pts[k];
+                    if (j > 0 && j < s_cnt[i] - 1) {
+                        float2 Ap = s_pts[k - 1], An = s_pts[k + 1];
+                        A.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.x, An.x),
+                                        __fmul_rn(a.lap_keep, A.x));
+                        A.y = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.y, An.y),
+                                        __fmul_rn(a.lap_keep, A.y));
+                    }
+                    keep[q] = A;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kPerThread; ++q) {
+                int k = tid + q * kStepThreads;
+                if (k < np) {
+                    s_pts[k] = keep[q];
+                    if (!(MODE & kModeResample)) a.pts_out[region + p0 + k] = keep[q];
+                }
+            }
+            if (!(MODE & kModeResample))
+                for (int i = b0 + tid; i < b1; i += kStepThreads) a.cnt_out[e0 + i] = s_cnt[i];
+            __syncthreads();
+        }
+
+        if (MODE & kModeResample) {
+            // arc length by sequential summation from the source, one thread per polyline
+            for (int i = b0 + tid; i < b1; i += kStepThreads) {
+                int q = s_loc[i] - p0, n = s_cnt[i];
+                float c = 0.0f;
+                s_cum[q] = 0.0f;
+                for (int s = 1; s < n; ++s) {
+                    c = __fadd_rn(c, seg_len(s_pts[q + s - 1], s_pts[q + s]));
+                    s_cum[q + s] = c;
+                }
+                s_len[i] = c;
+                s_nn[i] = new_count(c, a);
+            }
+            __syncthreads();
+            block_scan_excl(s_nn + b0, s_locn + b0, b1 - b0, s_wtot);
+            const int nout = s_locn[b1];
+            // one thread per output point: uniform arc-length positions
+            for (int o = tid; o < nout; o += kStepThreads) {
+                int i = find_slot(s_locn, b0, b1, o);
+                int j = o - s_locn[i];
+                int m = s_nn[i];
+                int q = s_loc[i] - p0, n = s_cnt[i];
+                float2 R;
+                if (j == 0) {
+                    R = s_pts[q];
+                } else if (j == m - 1) {
+                    R = s_pts[q + n - 1];
+                } else {
+                    float L = s_len[i];
+                    if (L == 0.0f) {
+                        R = s_pts[q];
+                    } else {
+                        float t = __fdiv_rn(__fmul_rn((float)j, L), (float)(m - 1));
+                        int lo = 1, hi = n - 1;
+                        while (lo < hi) {
+                            int mid = (lo + hi) >> 1;
+                            if (s_cum[q + mid] > t) hi = mid; else lo = mid + 1;
+                        }
+                        float c0 = s_cum[q + lo - 1];
+                        float seg = __fsub_rn(s_cum[q + lo], c0);
+                        float f = seg > 0.0f ? __fdiv_rn(__fsub_rn(t, c0), seg) : 0.0f;
+                        f = fminf(fmaxf(f, 0.0f), 1.0f);
+                        float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
+                        R = make_float2(lerp_rn(A.x, B.x, f), lerp_rn(A.y, B.y, f));
+                    }
+                }
+                a.pts_out[region + out_base + o] = R;
+                // splat: the point adds its edge weight to its group's cell (Eq. 1, Eq. 3)
+                int w = s_w[i];
+                if (w != 0) {
+                    int cx = min(max((int)floorf(R.x), 0), a.W - 1);
+                    int cy = min(max((int)floorf(R.y), 0), a.H - 1);
+                    atomicAdd(a.hist + (size_t)s_grp[i] * C + (size_t)cy * a.W + cx,
+                              (unsigned)w);
+                }
+            }
+            for (int i = b0 + tid; i < b1; i += kStepThreads) a.cnt_out[e0 + i] = s_nn[i];
+            if (tid == 0 && a.n_splat) atomicAdd(a.n_splat, (unsigned long long)nout);
+            out_base += nout;
+            __syncthreads();
+        }
+        b0 = b1;
+    }
+}
+
+template <typename T>
+cudaError_t launch_step_t(int mode, const StepArgs& a, cudaStream_t st) {
+    if (a.E <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((a.E + kEdgesPerBlock - 1) / kEdgesPerBlock));
+    switch (mode) {
+        case kModeResample: k_step<kModeResample, T><<<grid, kStepThreads, 0, st>>>(a); break;
+        case kModeAdvect: k_step<kModeAdvect, T><<<grid, kStepThreads, 0, st>>>(a); break;
+        case kModeAdvectResample:
+            k_step<kModeAdvectResample, T><<<grid, kStepThreads, 0, st>>>(a);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- init / fetch helpers
+
+// Spatial key of an edge: group, then the Morton index of its midpoint's cell
+// on a 64 x 64 tiling of the grid. Sorting by it gives each block of slots
+// nearby edges of one group (locality for the density gathers and the splat).
+__global__ void k_edge_keys(const float2* __restrict__ src, const float2* __restrict__ dst,
+                            const int32_t* __restrict__ group, int64_t E, int32_t W, int32_t H,
+                            uint32_t* key, uint32_t* bucket_cnt) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    float mx = 0.5f * (src[e].x + dst[e].x), my = 0.5f * (src[e].y + dst[e].y);
+    uint32_t tx = (uint32_t)min(max((int)(mx * 64.0f / (float)W), 0), 63);
+    uint32_t ty = (uint32_t)min(max((int)(my * 64.0f / (float)H), 0), 63);
+    uint32_t m = 0;
+    for (int b = 0; b < 6; ++b) m |= (((tx >> b) & 1u) << (2 * b)) | (((ty >> b) & 1u) << (2 * b + 1));
+    uint32_t k = (uint32_t)group[e] * 4096u + m;
+    key[e] = k;
+    atomicAdd(bucket_cnt + k, 1u);
+}
+
+// In-place exclusive scan of n bucket counts by one block of 1024 threads.
+__global__ void k_bucket_scan(uint32_t* cnt, int32_t n) {
+    __shared__ uint32_t s_part[1024];
+    const int tid = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int lo = min(n, tid * per), hi = min(n, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += cnt[i];
+    s_part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < 1024; ++t) {
+            uint32_t v = s_part[t];
+            s_part[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    uint32_t run = s_part[tid];
+    for (int i = lo; i < hi; ++i) {
+        uint32_t v = cnt[i];
+        cnt[i] = run;
+        run += v;
+    }
+}
+
+__global__ void k_edge_scatter(const uint32_t* __restrict__ key, int64_t E, uint32_t* cursor,
+                               int32_t* perm) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    uint32_t slot = atomicAdd(cursor + key[e], 1u);
+    perm[slot] = (int32_t)e;
+}
+
+__global__ void k_gather_edges(const int32_t* __restrict__ perm, int64_t E,
+                               const int32_t* __restrict__ group_in,
+                               const int32_t* __restrict__ weight_in, int32_t* group_out,
+                               int32_t* weight_out) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E) return;
+    int32_t e = perm[s];
+    group_out[s] = group_in ? group_in[e] : 0;
+    weight_out[s] = weight_in ? weight_in[e] : 1;
+}
+
+// Straight edges (2 points each) into the block layout.
+__global__ void k_straight_layout(const int32_t* __restrict__ perm, int64_t E,
+                                  const float2* __restrict__ src, const float2* __restrict__ dst,
+                                  int32_t cap, int32_t* cnt, float2* pts) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E) return;
+    int32_t e = perm[s];
+    int64_t b = s / kEdgesPerBlock, i = s % kEdgesPerBlock;
+    float2* q = pts + b * kEdgesPerBlock * (int64_t)cap + 2 * i;
+    q[0] = src[e];
+    q[1] = dst[e];
+    cnt[s] = 2;
+}
+
+// Caller CSR polylines into the block layout: one block of slots per CTA.
+__global__ void k_polyline_layout(const int32_t* __restrict__ perm, int64_t E,
+                                  const int64_t* __restrict__ off, const float2* __restrict__ xy,
+                                  int32_t cap, int32_t* cnt, float2* pts) {
+    __shared__ int s_n[kEdgesPerBlock];
+    __shared__ int s_o[kEdgesPerBlock + 1];
+    __shared__ int s_wtot[32];
+    const int64_t s0 = (int64_t)blockIdx.x * kEdgesPerBlock;
+    const int nb = (int)min((int64_t)kEdgesPerBlock, E - s0);
+    const int tid = threadIdx.x;
+    if (tid < nb) {
+        int32_t e = perm[s0 + tid];
+        s_n[tid] = (int)(off[e + 1] - off[e]);
+    }
+    __syncthreads();
+    block_scan_excl(s_n, s_o, nb, s_wtot);
+    if (tid < nb) {
+        int32_t e = perm[s0 + tid];
+        float2* q = pts + (int64_t)blockIdx.x * kEdgesPerBlock * cap + s_o[tid];
+        for (int j = 0; j < s_n[tid]; ++j) q[j] = xy[off[e] + j];
+        cnt[s0 + tid] = s_n[tid];
+    }
+}
+
+__global__ void k_counts_to_caller(const int32_t* __restrict__ perm,
+                                   const int32_t* __restrict__ cnt, int64_t E, int64_t* off) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < E) off[perm[s]] = cnt[s];
+    if (s == 0) off[E] = 0;
+}
+
+// Three-phase exclusive scan of off[0..E] (int64) in place: block sums, scan of
+// the block sums by one block, then per-block scans.
+constexpr int kScanBlock = 1024;
+
+__device__ long long block_scan_ll(long long v, long long* tmp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long t = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        tmp[lane] = t;
+    }
+    __syncthreads();
+    long long r = (wid > 0 ? tmp[wid - 1] : 0) + x;  // inclusive
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_sums(const int64_t* __restrict__ v, int64_t n, int64_t* sums) {
+    __shared__ long long tmp[32];
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    long long x = i < n ? v[i] : 0;
+    long long inc = block_scan_ll(x, tmp);
+    if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = inc;
+}
+
+__global__ void k_scan_partials(int64_t* sums, int64_t nblk) {
+    __shared__ long long tmp[32];
+    long long carry = 0;
+    for (int64_t base = 0; base < nblk; base += kScanBlock) {
+        int64_t i = base + threadIdx.x;
+        long long x = i < nblk ? sums[i] : 0;
+        long long inc = block_scan_ll(x, tmp);
+        if (i < nblk) sums[i] = carry + inc - x;
+        __shared__ long long s_last;
+        if (threadIdx.x == kScanBlock - 1) s_last = inc;
+        __syncthreads();
+        carry += s_last;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_apply(int64_t* v, int64_t n, const int64_t* sums) {
+    __shared__ long long tmp[32];
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    long long x = i < n ? v[i] : 0;
+    long long inc = block_scan_ll(x, tmp);
+    if (i < n) v[i] = sums[blockIdx.x] + inc - x;
+}
+
+__global__ void k_layout_to_caller(const int32_t* __restrict__ perm,
+                                   const int32_t* __restrict__ cnt,
+                                   const float2* __restrict__ pts, int64_t E, int32_t cap,
+                                   const int64_t* __restrict__ off, float2* xy, int32_t to_world,
+                                   float ox, float oy, float inv_scale, float xmin, float ymin) {
+    __shared__ int s_n[kEdgesPerBlock];
+    __shared__ int s_o[kEdgesPerBlock + 1];
+    __shared__ int s_wtot[32];
+    const int64_t s0 = (int64_t)blockIdx.x * kEdgesPerBlock;
+    const int nb = (int)min((int64_t)kEdgesPerBlock, E - s0);
+    const int tid = threadIdx.x;
+    if (tid < nb) s_n[tid] = cnt[s0 + tid];
+    __syncthreads();
+    block_scan_excl(s_n, s_o, nb, s_wtot);
+    if (tid < nb) {
+        int32_t e = perm[s0 + tid];
+        const float2* q = pts + (int64_t)blockIdx.x * kEdgesPerBlock * cap + s_o[tid];
+        float2* d = xy + off[e];
+        for (int j = 0; j < s_n[tid]; ++j) {
+            float2 p = q[j];
+            if (to_world) {
+                // presentation transform back to world units (not part of the method)
+                p.x = (p.x - ox) * inv_scale + xmin;
+                p.y = (p.y - oy) * inv_scale + ymin;
+            }
+            d[j] = p;
+        }
+    }
+}
+
+__global__ void k_sum_counts(const int32_t* __restrict__ cnt, int64_t E,
+                             unsigned long long* total) {
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s += (unsigned)cnt[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_step(int mode, int rho_dtype, const StepArgs& a, cudaStream_t st) {
+    switch (rho_dtype) {
+        case 0: return launch_step_t<float>(mode, a, st);
+        case 1: return launch_step_t<__nv_bfloat16>(mode, a, st);
+        case 2: return launch_step_t<__half>(mode, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_edge_keys(const float2* src, const float2* dst, const int32_t* group,
+                             int64_t E, int32_t W, int32_t H, uint32_t* key, uint32_t* bucket_cnt,
+                             cudaStream_t st) {
+    k_edge_keys<<<blocks_for(E, 256), 256, 0, st>>>(src, dst, group, E, W, H, key, bucket_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_scan(uint32_t* cnt, int32_t n_buckets, cudaStream_t st) {
+    k_bucket_scan<<<1, 1024, 0, st>>>(cnt, n_buckets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_scatter(const uint32_t* key, int64_t E, uint32_t* cursor, int32_t* perm,
+                                cudaStream_t st) {
+    k_edge_scatter<<<blocks_for(E, 256), 256, 0, st>>>(key, E, cursor, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_edges(const int32_t* perm, int64_t E, const int32_t* group_in,
+                                const int32_t* weight_in, int32_t* group_out,
+                                int32_t* weight_out, cudaStream_t st) {
+    k_gather_edges<<<blocks_for(E, 256), 256, 0, st>>>(perm, E, group_in, weight_in, group_out,
+                                                       weight_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_straight_layout(const int32_t* perm, int64_t E, const float2* src,
+                                   const float2* dst, int32_t cap, int32_t* cnt, float2* pts,
+                                   cudaStream_t st) {
+    k_straight_layout<<<blocks_for(E, 256), 256, 0, st>>>(perm, E, src, dst, cap, cnt, pts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_polyline_layout(const int32_t* perm, int64_t E, const int64_t* off,
+                                   const float2* xy, int32_t cap, int32_t* cnt, float2* pts,
+                                   cudaStream_t st) {
+    k_polyline_layout<<<blocks_for(E, kEdgesPerBlock), kEdgesPerBlock, 0, st>>>(perm, E, off, xy,
+                                                                               cap, cnt, pts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counts_to_caller(const int32_t* perm, const int32_t* cnt, int64_t E,
+                                    int64_t* off_out, cudaStream_t st) {
+    k_counts_to_caller<<<blocks_for(E, 256), 256, 0, st>>>(perm, cnt, E, off_out);
+    return cudaGetLastError();
+}
+
+size_t scan_offsets_tmp_elems(int64_t E) { return (size_t)((E + 1 + kScanBlock - 1) / kScanBlock); }
+
+cudaError_t launch_scan_offsets(int64_t* off, int64_t E, int64_t* tmp, cudaStream_t st) {
+    int64_t n = E + 1;
+    int64_t nblk = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_sums<<<(unsigned)nblk, kScanBlock, 0, st>>>(off, n, tmp);
+    k_scan_partials<<<1, kScanBlock, 0, st>>>(tmp, nblk);
+    k_scan_apply<<<(unsigned)nblk, kScanBlock, 0, st>>>(off, n, tmp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_layout_to_caller(const int32_t* perm, const int32_t* cnt, const float2* pts,
+                                    int64_t E, int32_t cap, const int64_t* off, float2* xy_out,
+                                    int32_t to_world, float ox, float oy, float inv_scale,
+                                    float xmin, float ymin, cudaStream_t st) {
+    k_layout_to_caller<<<blocks_for(E, kEdgesPerBlock), kEdgesPerBlock, 0, st>>>(
+        perm, cnt, pts, E, cap, off, xy_out, to_world, ox, oy, inv_scale, xmin, ymin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_counts(const int32_t* cnt, int64_t E, unsigned long long* total,
+                              cudaStream_t st) {
+    unsigned nblk = blocks_for(E, 256);
+    k_sum_counts<<<nblk < 1024u ? nblk : 1024u, 256, 0, st>>>(cnt, E, total);
+    return cudaGetLastError();
+}
+
+}  // namespace heb

@@ -1,0 +1,261 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on seeded synthetic graphs.
+
+Sizes span several blocks of 128 edges plus a ragged tail and finish in seconds on the
+oracle. Integer stages are bit-exact; floating-point stages are within the stated bounds:
+ - density rho: one rounding of an exact integer to FP32 plus one FP32 division,
+   |rho_gpu - rho| <= 4 ulp(rho) (relative 2^-21);
+ - positions in lockstep: 1e-5 of the grid extent, with every larger difference traced to a
+   verified near-tie decision (see parity.advect_mismatch);
+ - free-running positions: RMS within 1e-4 of the layout extent (spec tolerance), the
+   maximum reported.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected only on GPU machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1504_02687_gb300 as pkg  # noqa: E402
+from paper_1504_02687_gb300 import synth  # noqa: E402
+
+from parity import (advect_mismatch, fetch_px, oracle_params, params_for,  # noqa: E402
+                    resample_mismatch, rho_as_f64, step_h, sums_as_i64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1504_02687_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+WORKLOADS = {
+    "g1-fixed32": dict(seed=11, n_edges=1000, n_groups=1, grid=(96, 80), radius=3, passes=3,
+                       n_fixed=32),
+    "g3-bylength-weighted": dict(seed=12, n_edges=777, n_groups=3, grid=(128, 96), radius=4,
+                                 passes=3, n_fixed=0, n_max=24, weighted=True),
+    "g5-bylength-r2k4": dict(seed=13, n_edges=300, n_groups=5, grid=(64, 64), radius=2, passes=4,
+                             n_fixed=0, n_max=16, delta=1.5),
+}
+
+
+def _make(name, **over):
+    w = synth.tiny(**WORKLOADS[name])
+    p = params_for(w, **over)
+    ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    return w, p, ctx
+
+
+def test_grid_map_matches_oracle_bit_for_bit():
+    w, p, ctx = _make("g3-bylength-weighted")
+    try:
+        off, xy = pkg.bundle_fetch(ctx, pixels=True)
+        W, H, mp, sp, dp = oracle.grid_map(w.src_xy, w.dst_xy, w.grid[0], w.grid[1],
+                                           margin=p.radius)
+        np.testing.assert_array_equal(np.diff(off), 2)
+        np.testing.assert_array_equal(xy[0::2], sp)
+        np.testing.assert_array_equal(xy[1::2], dp)
+        info = pkg.bundle_get_info(ctx)
+        assert list(info.map) == list(mp)
+        # world coordinates come back through the inverse map
+        off2, xyw = pkg.bundle_fetch(ctx)
+        np.testing.assert_allclose(xyw[0::2], w.src_xy, atol=1e-5)
+    finally:
+        pkg.bundle_destroy(ctx)
+
+
+def _lockstep_once(ctx, w, p):
+    """One GPU iteration from the GPU's current state, every stage checked against the oracle."""
+    info = pkg.bundle_get_info(ctx)
+    it = info.iteration
+    off0, P0 = fetch_px(ctx)
+    pkg.bundle_iterate(ctx, 1)
+    offR, R = fetch_px(ctx, resampled=True)
+    hist = pkg.bundle_fetch_density(ctx, pkg.DENSITY_HIST).astype(np.int64)
+    S = sums_as_i64(ctx)
+    rho = rho_as_f64(ctx)
+    off1, P1 = fetch_px(ctx)
+    G, H, W = hist.shape
+    extent = max(W, H)
+    # resampling (Sec. 2.1): counts exact up to verified ties, positions to FP32 rounding
+    n_cnt, n_cnt_bad, worst = resample_mismatch(off0, P0, offR, R, p, 0)
+    assert n_cnt_bad == 0
+    # FP32 arc-length sums: a few ulps of the extent per point of the polyline
+    assert worst <= 8 * max(p.n_fixed, p.n_max) * 2.0 ** -23 * extent, worst
+    # histogram of the GPU's resampled points (Eq. 1, Eq. 3): bit for bit
+    group = w.group
+    np.testing.assert_array_equal(hist, oracle.splat(offR, R, group, w.weight, G, H, W))
+    assert hist.sum() == (np.diff(offR) * (w.weight if w.weight is not None else 1)).sum()
+    # box passes (Sec. 3.1): bit for bit
+    np.testing.assert_array_equal(S, oracle.smooth(hist, p.radius, p.passes))
+    # layer mix (Eq. 3, Eq. 4): exact integer numerator, one FP32 rounding and division
+    rho_o = oracle.combine(S, p.radius, p.passes, p.alpha_num, p.alpha_den)
+    rel, absl = {pkg.RHO_F32: (2.0 ** -21, 1e-35), pkg.RHO_BF16: (2.0 ** -8, 1e-35),
+                 pkg.RHO_F16: (2.0 ** -10, 2.0 ** -24)}[info.rho_dtype]
+    np.testing.assert_array_less(np.abs(rho - rho_o), rel * np.abs(rho_o) + absl)
+    # advection + Laplacian (Eq. 5, Sec. 3.3) from the GPU's R and rho
+    h = step_h(p, it)
+    n_bad, n_unexp, P_o = advect_mismatch(offR, R, group, rho, h, p, P1, 1e-5 * extent)
+    assert n_unexp == 0, (n_bad, n_unexp)
+    assert n_bad <= max(3, 1e-3 * len(R))
+    np.testing.assert_array_equal(np.diff(off1), np.diff(offR))
+    # endpoints never move
+    np.testing.assert_array_equal(P1[off1[:-1]], P0[off0[:-1]])
+    np.testing.assert_array_equal(P1[off1[1:] - 1], P0[off0[1:] - 1])
+    return n_bad, n_cnt
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_lockstep_stages(name):
+    w, p, ctx = _make(name)
+    try:
+        _lockstep_once(ctx, w, p)          # iteration 0, from straight edges
+        pkg.bundle_iterate(ctx, 2)
+        _lockstep_once(ctx, w, p)          # iteration 3, from bundled polylines
+    finally:
+        pkg.bundle_destroy(ctx)
+
+
+@pytest.mark.parametrize("rho_dtype", [pkg.RHO_BF16, pkg.RHO_F16])
+def test_lockstep_reduced_precision_density(rho_dtype):
+    """BF16/FP16 storage of rho: the integer stages stay bit-exact; the stored density is the
+    exact value rounded once more to the storage type; advection is checked from it."""
+    w, p, ctx = _make("g3-bylength-weighted", rho_dtype=rho_dtype)
+    try:
+        pkg.bundle_iterate(ctx, 1)
+        S = sums_as_i64(ctx)
+        rho = rho_as_f64(ctx)
+        rho_o = oracle.combine(S, p.radius, p.passes, p.alpha_num, p.alpha_den)
+        rel, absl = (2.0 ** -8, 1e-35) if rho_dtype == pkg.RHO_BF16 else (2.0 ** -10, 2.0 ** -24)
+        np.testing.assert_array_less(np.abs(rho - rho_o), rel * np.abs(rho_o) + absl)
+        _lockstep_once(ctx, w, p)
+    finally:
+        pkg.bundle_destroy(ctx)
+
+
+def test_fused_sequence_equals_split_and_resume():
+    """The fused advect -> resample -> splat kernel used inside one bundle_iterate(n) gives the
+    same bits as n single iterations, and as a context resumed from fetched polylines."""
+    w = synth.tiny(**WORKLOADS["g3-bylength-weighted"])
+    p = params_for(w)
+    a = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    b = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    try:
+        pkg.bundle_iterate(a, 2)
+        mid_off, mid_xy = pkg.bundle_fetch(a, pixels=True)
+        pkg.bundle_iterate(a, 3)
+        for _ in range(5):
+            pkg.bundle_iterate(b, 1)
+        oa, xa = pkg.bundle_fetch(a, pixels=True)
+        ob, xb = pkg.bundle_fetch(b, pixels=True)
+        np.testing.assert_array_equal(oa, ob)
+        np.testing.assert_array_equal(xa, xb)
+        for which in (pkg.DENSITY_HIST, pkg.DENSITY_SUMS, pkg.DENSITY_RHO):
+            np.testing.assert_array_equal(pkg.bundle_fetch_density(a, which),
+                                          pkg.bundle_fetch_density(b, which))
+        info = pkg.bundle_get_info(a)
+        c = pkg.bundle_init_polylines(params_for(w), mid_off, mid_xy, w.group, w.n_groups,
+                                      w.weight, map5=np.array(info.map), iteration=2)
+        try:
+            pkg.bundle_iterate(c, 3)
+            oc, xc = pkg.bundle_fetch(c, pixels=True)
+            np.testing.assert_array_equal(oc, oa)
+            np.testing.assert_array_equal(xc, xa)
+        finally:
+            pkg.bundle_destroy(c)
+    finally:
+        pkg.bundle_destroy(a)
+        pkg.bundle_destroy(b)
+
+
+def test_free_running_small_config():
+    """The small configuration (2,000 edges, 256^2, r = 4, k = 3, 32 points, 10 iterations):
+    GPU FP32 vs FP64 oracle after all iterations."""
+    w = synth.small()
+    p = params_for(w)
+    ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    try:
+        off0, P0 = fetch_px(ctx)
+        pkg.bundle_iterate(ctx, w.iters)
+        off, P = fetch_px(ctx)
+    finally:
+        pkg.bundle_destroy(ctx)
+    res = oracle.run(off0, P0, w.group, w.weight, 1, 256, 256, oracle_params(p), 0, w.iters)
+    np.testing.assert_array_equal(off, res.off)
+    err = np.hypot(*(P - res.xy).T) / 256.0
+    rms = float(np.sqrt((err ** 2).mean()))
+    print(f"free-running small: max {err.max():.3e} rms {rms:.3e} (units of the extent)")
+    assert rms <= 1e-4
+    assert np.mean(err > 1e-4) < 0.01
+
+
+def test_edge_cases():
+    # one edge; an edge on the border; maximum radius; 64 groups with few edges; int64 sums
+    # forced on a small case; zero weights
+    rng = np.random.default_rng(99)
+    cases = []
+    cases.append((np.array([[0.1, 0.2]], np.float32), np.array([[0.9, 0.7]], np.float32), None,
+                  1, None, dict(grid_w=32, grid_h=32, radius=2, n_fixed=8)))
+    E = 130
+    s = rng.uniform(0, 1, (E, 2)).astype(np.float32)
+    d = rng.uniform(0, 1, (E, 2)).astype(np.float32)
+    s[:10, 0] = 0.0
+    d[:10, 0] = 0.0
+    cases.append((s, d, (np.arange(E) % 64).astype(np.int32), 64, None,
+                  dict(grid_w=40, grid_h=24, radius=23, margin_px=0, n_fixed=0, n_max=12)))
+    wts = rng.integers(0, 3, E).astype(np.int32)
+    cases.append((s, d, None, 1, wts, dict(grid_w=50, grid_h=70, radius=3, sum_bits=64,
+                                           n_fixed=6)))
+    for (src, dst, g, G, wt, over) in cases:
+        p = pkg.default_params(**over)
+        ctx = pkg.bundle_init(p, src, dst, g, G, wt)
+        try:
+            class Wk:
+                group, weight = g, wt
+            _lockstep_once(ctx, Wk, p)
+            _lockstep_once(ctx, Wk, p)
+        finally:
+            pkg.bundle_destroy(ctx)
+
+
+def test_device_inputs_and_outputs():
+    w = synth.tiny(**WORKLOADS["g1-fixed32"])
+    p = params_for(w)
+    dev = torch.device("cuda:0")
+    ctx_h = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    ctx_d = pkg.bundle_init(p, torch.from_numpy(w.src_xy).to(dev), torch.from_numpy(w.dst_xy).to(dev),
+                            torch.from_numpy(w.group).to(dev), w.n_groups, None,
+                            stream=torch.cuda.current_stream())
+    try:
+        pkg.bundle_iterate(ctx_h, 2)
+        pkg.bundle_iterate(ctx_d, 2)
+        off_h, xy_h = pkg.bundle_fetch(ctx_h)
+        info = pkg.bundle_get_info(ctx_d)
+        off_d = torch.zeros(info.n_edges + 1, dtype=torch.int64, device=dev)
+        xy_d = torch.zeros((info.n_points, 2), dtype=torch.float32, device=dev)
+        pkg.bundle_fetch(ctx_d, off=off_d, xy=xy_d)
+        np.testing.assert_array_equal(off_d.cpu().numpy(), off_h)
+        np.testing.assert_array_equal(xy_d.cpu().numpy(), xy_h)
+    finally:
+        pkg.bundle_destroy(ctx_h)
+        pkg.bundle_destroy(ctx_d)
+
+
+def test_profile_counts_launches():
+    w, p, ctx = _make("g1-fixed32")
+    try:
+        pkg.bundle_profile_enable(ctx, True)
+        pkg.bundle_iterate(ctx, 3)
+        prof = pkg.bundle_profile_read(ctx)
+        assert prof["resample"][1] == 1
+        assert prof["advect_resample"][1] == 2
+        assert prof["advect"][1] == 1
+        assert prof["rowbox"][1] == prof["colbox"][1] == prof["combine"][1] == 3
+        assert all(ms >= 0 for ms, _ in prof.values())
+    finally:
+        pkg.bundle_destroy(ctx)
