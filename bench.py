@@ -288,7 +288,7 @@ def run_ours(args):
     b_rho = 4 if args.rho == "f32" else 2
 
     clocks = ClockSampler(dev_index)
-    pkg.bundle_iterate(ctx, max(args.warmup, 3) if args.warmup >= 3 else args.warmup)
+    pkg.bundle_iterate(ctx, args.warmup)
     pkg.bundle_sync(ctx)
     done0 = pkg.bundle_get_info(ctx).points_processed
     pkg.bundle_profile_enable(ctx, True)

@@ -173,25 +173,56 @@ def test_fused_sequence_equals_split_and_resume():
         pkg.bundle_destroy(b)
 
 
+def _ulp_perturbed(xy, seed):
+    """Move every coordinate by -1, 0 or +1 FP32 ulp (seeded)."""
+    rng = np.random.default_rng(seed)
+    x32 = xy.astype(np.float32)
+    d = rng.integers(-1, 2, x32.shape)
+    up, dn = np.nextafter(x32, np.float32(1e9)), np.nextafter(x32, np.float32(-1e9))
+    return np.where(d > 0, up, np.where(d < 0, dn, x32)).astype(np.float64)
+
+
 def test_free_running_small_config():
-    """The small configuration (2,000 edges, 256^2, r = 4, k = 3, 32 points, 10 iterations):
-    GPU FP32 vs FP64 oracle after all iterations."""
+    """The small configuration (2,000 edges, 256^2, r = 4, k = 3, 32 points, 10 iterations),
+    GPU FP32 vs FP64 oracle from the same start.
+
+    After one iteration the RMS position error is within 1e-4 of the extent. Over many
+    iterations the method itself amplifies ulp-level differences through its discrete
+    decisions (cell of a point, accepted step): two FP64 oracle runs whose endpoints differ
+    by +-1 FP32 ulp drift apart by ~2e-3 of the extent RMS after 10 iterations. The GPU must
+    stay inside that envelope of the method's own sensitivity."""
     w = synth.small()
     p = params_for(w)
     ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
     try:
         off0, P0 = fetch_px(ctx)
-        pkg.bundle_iterate(ctx, w.iters)
+        pkg.bundle_iterate(ctx, 1)
+        off1, P1 = fetch_px(ctx)
+        pkg.bundle_iterate(ctx, w.iters - 1)
         off, P = fetch_px(ctx)
     finally:
         pkg.bundle_destroy(ctx)
-    res = oracle.run(off0, P0, w.group, w.weight, 1, 256, 256, oracle_params(p), 0, w.iters)
+    prm = oracle_params(p)
+    one = oracle.run(off0, P0, w.group, w.weight, 1, 256, 256, prm, 0, 1)
+    err1 = np.hypot(*(P1 - one.xy).T) / 256.0
+    rms1 = float(np.sqrt((err1 ** 2).mean()))
+    assert rms1 <= 1e-4, rms1
+    res = oracle.run(off0, P0, w.group, w.weight, 1, 256, 256, prm, 0, w.iters)
     np.testing.assert_array_equal(off, res.off)
     err = np.hypot(*(P - res.xy).T) / 256.0
     rms = float(np.sqrt((err ** 2).mean()))
-    print(f"free-running small: max {err.max():.3e} rms {rms:.3e} (units of the extent)")
-    assert rms <= 1e-4
-    assert np.mean(err > 1e-4) < 0.01
+    env_rms, env_max = [], []
+    for seed in (0, 1):
+        alt = oracle.run(off0, _ulp_perturbed(P0, seed), w.group, w.weight, 1, 256, 256, prm, 0,
+                         w.iters)
+        e = np.hypot(*(alt.xy - res.xy).T) / 256.0
+        env_rms.append(float(np.sqrt((e ** 2).mean())))
+        env_max.append(float(e.max()))
+    print(f"free-running small: 1 iteration rms {rms1:.2e} max {err1.max():.2e}; "
+          f"{w.iters} iterations rms {rms:.2e} max {err.max():.2e}; FP64 +-1ulp envelope rms "
+          f"{env_rms} max {env_max} (units of the extent)")
+    assert rms <= 1.5 * max(env_rms)
+    assert err.max() <= 1.5 * max(env_max)
 
 
 def test_edge_cases():
