@@ -69,7 +69,7 @@ def test_grid_map_matches_oracle_bit_for_bit():
         pkg.bundle_destroy(ctx)
 
 
-def _lockstep_once(ctx, w, p):
+def _lockstep_once(ctx, w, p, max_bad_frac=1e-3):
     """One GPU iteration from the GPU's current state, every stage checked against the oracle."""
     info = pkg.bundle_get_info(ctx)
     it = info.iteration
@@ -102,7 +102,7 @@ def _lockstep_once(ctx, w, p):
     h = step_h(p, it)
     n_bad, n_unexp, P_o = advect_mismatch(offR, R, group, rho, h, p, P1, 1e-5 * extent)
     assert n_unexp == 0, (n_bad, n_unexp)
-    assert n_bad <= max(3, 1e-3 * len(R))
+    assert n_bad <= max(3, max_bad_frac * len(R))
     np.testing.assert_array_equal(np.diff(off1), np.diff(offR))
     # endpoints never move
     np.testing.assert_array_equal(P1[off1[:-1]], P0[off0[:-1]])
@@ -248,8 +248,10 @@ def test_edge_cases():
         try:
             class Wk:
                 group, weight = g, wt
-            _lockstep_once(ctx, Wk, p)
-            _lockstep_once(ctx, Wk, p)
+            # a radius near the grid size makes the density almost flat: many directions are
+            # ill-conditioned in FP32; each such mismatch must still be a verified ambiguity
+            _lockstep_once(ctx, Wk, p, max_bad_frac=0.05)
+            _lockstep_once(ctx, Wk, p, max_bad_frac=0.05)
         finally:
             pkg.bundle_destroy(ctx)
 
