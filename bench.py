@@ -279,7 +279,9 @@ def run_ours(args):
     lib_build.build()
     # every rank bundles its own graph of the same configuration (independent problems)
     w = make_workload(args.workload, args.edges, seed_offset=rank * 1000)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it and the timing events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     p = params_of(w, args.rho)
     ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight, stream=stream)
     info = pkg.bundle_get_info(ctx)

@@ -148,12 +148,17 @@ def _host(a, dtype):
     return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 
 
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy: the legacy default stream
+
+
 def _stream_handle(stream):
+    """cudaStream_t of a torch stream or a raw handle. torch's default stream has handle 0,
+    which the library would read as "make your own stream"; it is passed as
+    cudaStreamLegacy instead so the work really runs on the caller's stream."""
     if stream is None:
         return None
-    if hasattr(stream, "cuda_stream"):
-        return ctypes.c_void_p(stream.cuda_stream)
-    return ctypes.c_void_p(int(stream))
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return ctypes.c_void_p(h if h else _CUDA_STREAM_LEGACY)
 
 
 def bundle_init(params: BundleParams, src_xy, dst_xy, group=None, n_groups=1, weight=None,
