@@ -148,6 +148,8 @@ def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho):
         return 2 * GC * b_sum
     if kind == "combine":
         return GC * (b_sum + b_rho)
+    if kind == "quads":
+        return GC * b_rho * 5
     return 0
 
 
@@ -341,7 +343,8 @@ def run_ours(args):
     step_bytes = (algorithmic_bytes("advect_resample", N_avg, E, GC, b_sum, b_rho)
                   + algorithmic_bytes("rowbox", N_avg, E, GC, b_sum, b_rho)
                   + algorithmic_bytes("colbox", N_avg, E, GC, b_sum, b_rho)
-                  + algorithmic_bytes("combine", N_avg, E, GC, b_sum, b_rho))
+                  + algorithmic_bytes("combine", N_avg, E, GC, b_sum, b_rho)
+                  + algorithmic_bytes("quads", N_avg, E, GC, b_sum, b_rho))
     pkg.bundle_destroy(ctx)
 
     out = {

@@ -175,9 +175,9 @@ bundle_status bundle_get_info(const bundle_ctx* ctx, bundle_info* out);
  * every launch of bundle_iterate (a tracing aid; off by default, adds two event
  * records per launch). Kinds, in order: 0 resample+splat, 1 advect+Laplacian,
  * 2 advect+Laplacian+resample+splat, 3 row box passes, 4 column box passes,
- * 5 layer mix, 6 histogram clear.
+ * 5 layer mix, 6 histogram clear, 7 density quad build.
  */
-#define BUNDLE_PROFILE_KINDS 7
+#define BUNDLE_PROFILE_KINDS 8
 bundle_status bundle_profile_enable(bundle_ctx* ctx, int32_t on);
 
 /*

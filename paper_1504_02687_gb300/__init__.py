@@ -27,7 +27,7 @@ INPUT_DEVICE = 1
 FETCH_DEVICE, FETCH_PIXELS, FETCH_RESAMPLED = 1, 2, 4
 DENSITY_HIST, DENSITY_SUMS, DENSITY_RHO = 0, 1, 2
 PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "combine",
-                 "hist_clear")
+                 "hist_clear", "quads")
 
 EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bundle_iterate",
             "bundle_fetch", "bundle_fetch_density", "bundle_get_info", "bundle_sync",

@@ -41,6 +41,7 @@ struct bundle_ctx {
     void* Y = nullptr;
     void* S = nullptr;
     void* rho = nullptr;
+    void* quads = nullptr;
     unsigned long long* counters = nullptr;  // [0] points splatted in total, [1] scratch sum
     int64_t* fetch_off = nullptr;
     int64_t* fetch_tmp = nullptr;
@@ -109,7 +110,7 @@ void free_ctx(bundle_ctx* c) {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->perm, c->group, c->weight, c->cnt[0], c->cnt[1], c->pts[0], c->pts[1],
-                    c->hist, c->Y, c->S, c->rho, c->counters, c->fetch_off, c->fetch_tmp,
+                    c->hist, c->Y, c->S, c->rho, c->quads, c->counters, c->fetch_off, c->fetch_tmp,
                     c->fetch_xy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -308,6 +309,8 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->Y), C * sb));
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->S), C * sb));
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->rho), C * rho_bytes(c->p.rho_dtype)));
+    CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->quads),
+                       (size_t)c->G * quad_elems(c->W, c->H) * 4 * rho_bytes(c->p.rho_dtype)));
     CUDA_TRY(e, dalloc(c, &c->counters, 4));
     CUDA_TRY(e, dalloc(c, &c->fetch_off, (size_t)E + 1));
     CUDA_TRY(e, dalloc(c, &c->fetch_tmp, scan_offsets_tmp_elems(E) + 1));
@@ -410,7 +413,7 @@ bool to_host(const T* p, int64_t n, bool on_device, std::vector<T>* v, const T**
 }
 
 enum ProfileKind { kProfResample = 0, kProfAdvect, kProfAdvectResample, kProfRowbox,
-                   kProfColbox, kProfCombine, kProfHistClear, kProfKinds };
+                   kProfColbox, kProfCombine, kProfHistClear, kProfQuads, kProfKinds };
 
 // Launch through `fn`, bracketed by two events when profiling is on.
 template <typename F>
@@ -441,7 +444,7 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
     a.pts_out = c->pts[out];
     a.group = c->group;
     a.weight = c->weight;
-    a.rho = c->rho;
+    a.quads = c->quads;
     a.hist = c->hist;
     a.n_splat = c->counters;
     a.E = c->E;
@@ -474,6 +477,7 @@ bundle_status run_filter(bundle_ctx* c) {
     f.Y = c->Y;
     f.S = c->S;
     f.rho = c->rho;
+    f.quads = c->quads;
     f.G = c->G;
     f.H = c->H;
     f.W = c->W;
@@ -487,6 +491,7 @@ bundle_status run_filter(bundle_ctx* c) {
     CUDA_TRY(&c->err, timed(c, kProfCombine, [&] {
                  return launch_combine(c->sum_bits, c->p.rho_dtype, f, c->stream);
              }));
+    CUDA_TRY(&c->err, timed(c, kProfQuads, [&] { return launch_quads(c->p.rho_dtype, f, c->stream); }));
     return BUNDLE_OK;
 }
 

@@ -16,8 +16,8 @@ namespace heb {
 // counts are stored: a block recovers its edges' offsets with one scan.
 constexpr int kEdgesPerBlock = 128;
 constexpr int kStepThreads = 256;
-constexpr int kBatchPoints = 2048;  // points staged in shared memory per batch
-constexpr int kMaxCap = 256;        // largest polyline (n_fixed or n_max)
+constexpr int kBatchPoints = 3072;  // points staged in shared memory per batch
+constexpr int kMaxCap = 64;         // largest polyline (n_fixed or n_max): two warp rounds
 constexpr float kEdgeGuard = 0.0009765625f;  // positions stay below W - 2^-10
 
 enum StepMode : int {
@@ -33,7 +33,7 @@ struct StepArgs {
     float2* pts_out;         // output polylines (block layout)
     const int32_t* group;    // [E] per slot
     const int32_t* weight;   // [E] per slot
-    const void* rho;         // [G][H][W] density, element type per rho_dtype
+    const void* quads;       // [G][H+3][W+3] 2x2 density quads (see QuadMap), rho type
     uint32_t* hist;          // [G][H][W] histogram accumulated by the splat
     unsigned long long* n_splat;  // running count of splatted points
     int64_t E;
@@ -53,6 +53,7 @@ struct FilterArgs {
     void* Y;               // [G][H][W] row-filtered workspace (sum type)
     void* S;               // [G][H][W] smoothed sums (sum type)
     void* rho;             // [G][H][W] density (rho type)
+    void* quads;           // [G][H+3][W+3] density quads (rho type x 4)
     int32_t G, H, W, r, passes;
     int64_t mix_self;      // q (G - 1) + p : weight of a group's own layer
     int64_t mix_all;       // p : weight of the all-groups sum
@@ -60,11 +61,24 @@ struct FilterArgs {
     float den_f;           // q (G - 1) s^k (or s^k for one group), rounded to float
 };
 
+// Density quads. The gather side of the iteration reads the density through a
+// quad map: entry (a, b), for a in [-2, W] and b in [-2, H], holds the four
+// values {E(a,b), E(a+1,b), E(a,b+1), E(a+1,b+1)} of the reflection-extended
+// map E(a, b) = rho(refl(a), refl(b)) at quad index (b + 2) * (W + 3) + (a + 2).
+// One quad is the whole 2x2 footprint of a bilinear lookup; four quads hold
+// the 12 texels of the gradient stencil. No index reflection happens on the
+// gather side.
+constexpr int kQuadPad = 3;
+__host__ __device__ inline int64_t quad_elems(int W, int H) {
+    return (int64_t)(W + kQuadPad) * (H + kQuadPad);
+}
+
 // Launchers (return the launch status; nothing here synchronises).
 cudaError_t launch_step(int mode, int rho_dtype, const StepArgs& a, cudaStream_t st);
 cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st);
 
 // Init / fetch helpers (point layout <-> caller order).
 cudaError_t launch_edge_keys(const float2* src, const float2* dst, const int32_t* group,

@@ -148,6 +148,43 @@ __global__ void k_combine(const TS* __restrict__ S, R* __restrict__ rho, int G, 
     }
 }
 
+// ------------------------------------------------------------- density quads
+// Quad (a, b), a in [-2, W], b in [-2, H]: the 2x2 block of the reflection-
+// extended density with top-left corner (a, b), stored as one vector.
+template <typename R>
+__device__ __forceinline__ uint32_t pack2(R lo, R hi) {
+    unsigned short l = *reinterpret_cast<unsigned short*>(&lo);
+    unsigned short h = *reinterpret_cast<unsigned short*>(&hi);
+    return (uint32_t)l | ((uint32_t)h << 16);
+}
+
+template <typename R>
+__global__ void k_quads(const R* __restrict__ rho, R* __restrict__ quads, int G, int H, int W) {
+    const int64_t Wq = W + kQuadPad, QC = Wq * (H + kQuadPad);
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)G * QC) return;
+    const int64_t g = idx / QC, rem = idx % QC;
+    const int b = (int)(rem / Wq) - 2, a = (int)(rem % Wq) - 2;
+    const R* L = rho + g * (int64_t)H * W;
+    const int r0 = reflect_index(b, H) * W, r1 = reflect_index(b + 1, H) * W;
+    const int c0 = reflect_index(a, W), c1 = reflect_index(a + 1, W);
+    R e00 = L[r0 + c0], e10 = L[r0 + c1], e01 = L[r1 + c0], e11 = L[r1 + c1];
+    if constexpr (sizeof(R) == 4) {
+        reinterpret_cast<float4*>(quads)[idx] = make_float4(e00, e10, e01, e11);
+    } else {
+        reinterpret_cast<uint2*>(quads)[idx] = make_uint2(pack2(e00, e10), pack2(e01, e11));
+    }
+}
+
+template <typename R>
+cudaError_t quads_t(const FilterArgs& a, cudaStream_t st) {
+    const int64_t n = (int64_t)a.G * quad_elems(a.W, a.H);
+    k_quads<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(static_cast<const R*>(a.rho),
+                                                            static_cast<R*>(a.quads), a.G, a.H,
+                                                            a.W);
+    return cudaGetLastError();
+}
+
 template <typename TS>
 cudaError_t rowbox_t(const FilterArgs& a, cudaStream_t st) {
     const int c = (a.W + 31) / 32;
@@ -206,6 +243,15 @@ cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
 
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
     return sum_bits == 32 ? colbox_t<uint32_t>(a, st) : colbox_t<unsigned long long>(a, st);
+}
+
+cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st) {
+    switch (rho_dtype) {
+        case 0: return quads_t<float>(a, st);
+        case 1: return quads_t<__nv_bfloat16>(a, st);
+        case 2: return quads_t<__half>(a, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st) {

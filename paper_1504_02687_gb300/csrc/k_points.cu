@@ -11,43 +11,58 @@
 namespace heb {
 namespace {
 
-__device__ __forceinline__ int reflect_index(int i, int n) {
-    // half-sample symmetric reflection: -1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2
-    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
-}
-
+// One density quad as four floats (see the quad map in internal.cuh).
 template <typename T>
-__device__ __forceinline__ float load_rho(const T* p);
+__device__ __forceinline__ float4 load_quad(const T* Q, int64_t i);
 template <>
-__device__ __forceinline__ float load_rho<float>(const float* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float load_rho<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(p));
+__device__ __forceinline__ float4 load_quad<float>(const float* Q, int64_t i) {
+    return __ldg(reinterpret_cast<const float4*>(Q) + i);
 }
 template <>
-__device__ __forceinline__ float load_rho<__half>(const __half* p) {
-    return __half2float(__ldg(p));
+__device__ __forceinline__ float4 load_quad<__nv_bfloat16>(const __nv_bfloat16* Q, int64_t i) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(Q) + i);
+    __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+    __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+    float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 load_quad<__half>(const __half* Q, int64_t i) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(Q) + i);
+    __half2 lo = *reinterpret_cast<__half2*>(&u.x);
+    __half2 hi = *reinterpret_cast<__half2*>(&u.y);
+    float2 a = __half22float2(lo), b = __half22float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
 __device__ __forceinline__ float lerp_rn(float a, float b, float f) {
     return __fmaf_rn(f, __fsub_rn(b, a), a);
 }
 
-// Bilinear density of one layer at (x, y): cell centres sit at (a + 0.5, b + 0.5).
-template <typename T>
-__device__ __forceinline__ float density_at(const T* __restrict__ L, int W, int H, float x,
-                                            float y) {
+// Cell frame of a position: cell centres sit at (a + 0.5, b + 0.5). Positions stay in
+// [0, W - 2^-10]; the clamp keeps every quad index on the map regardless.
+struct Frame {
+    int a0, b0;
+    float fu, fv;
+};
+__device__ __forceinline__ Frame frame_of(float x, float y, int W, int H) {
     float u = __fsub_rn(x, 0.5f), v = __fsub_rn(y, 0.5f);
     float fa = floorf(u), fb = floorf(v);
-    // positions stay in [0, W - 2^-10]; the clamp keeps every index on the map regardless
-    int a0 = min(max((int)fa, -1), W - 1), b0 = min(max((int)fb, -1), H - 1);
-    float fu = __fsub_rn(u, fa), fv = __fsub_rn(v, fb);
-    int c0 = reflect_index(a0, W), c1 = reflect_index(a0 + 1, W);
-    const T* r0 = L + (size_t)reflect_index(b0, H) * W;
-    const T* r1 = L + (size_t)reflect_index(b0 + 1, H) * W;
-    float e00 = load_rho(r0 + c0), e10 = load_rho(r0 + c1);
-    float e01 = load_rho(r1 + c0), e11 = load_rho(r1 + c1);
-    return lerp_rn(lerp_rn(e00, e10, fu), lerp_rn(e01, e11, fu), fv);
+    Frame f;
+    f.a0 = min(max((int)fa, -1), W - 1);
+    f.b0 = min(max((int)fb, -1), H - 1);
+    f.fu = __fsub_rn(u, fa);
+    f.fv = __fsub_rn(v, fb);
+    return f;
+}
+
+// Bilinear density of one layer's quad map at (x, y).
+template <typename T>
+__device__ __forceinline__ float density_at(const T* __restrict__ Q, int W, int H, float x,
+                                            float y) {
+    Frame f = frame_of(x, y, W, H);
+    float4 q = load_quad(Q, (int64_t)(f.b0 + 2) * (W + kQuadPad) + (f.a0 + 2));
+    return lerp_rn(lerp_rn(q.x, q.y, f.fu), lerp_rn(q.z, q.w, f.fu), f.fv);
 }
 
 __device__ __forceinline__ float clamp_pos(float v, int n) {
@@ -60,32 +75,26 @@ __device__ __forceinline__ float clamp_pos(float v, int n) {
 // four surrounding cell centres on the reflection-extended map; the magnitude
 // starts at h and halves until the density is not lower than at x.
 template <typename T>
-__device__ float2 advect_point(float2 p, const T* __restrict__ L, int W, int H, float h,
+__device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, float h,
                                float eps, int tries) {
-    float u = __fsub_rn(p.x, 0.5f), v = __fsub_rn(p.y, 0.5f);
-    float fa = floorf(u), fb = floorf(v);
-    int a0 = min(max((int)fa, -1), W - 1), b0 = min(max((int)fb, -1), H - 1);
-    float fu = __fsub_rn(u, fa), fv = __fsub_rn(v, fb);
-    int cm = reflect_index(a0 - 1, W), c0 = reflect_index(a0, W);
-    int c1 = reflect_index(a0 + 1, W), c2 = reflect_index(a0 + 2, W);
-    const T* rm = L + (size_t)reflect_index(b0 - 1, H) * W;
-    const T* r0 = L + (size_t)reflect_index(b0, H) * W;
-    const T* r1 = L + (size_t)reflect_index(b0 + 1, H) * W;
-    const T* r2 = L + (size_t)reflect_index(b0 + 2, H) * W;
-    // 4 x 4 neighbourhood without its corners
-    float e0m = load_rho(rm + c0), e1m = load_rho(rm + c1);
-    float em0 = load_rho(r0 + cm), e00 = load_rho(r0 + c0), e10 = load_rho(r0 + c1),
-          e20 = load_rho(r0 + c2);
-    float em1 = load_rho(r1 + cm), e01 = load_rho(r1 + c0), e11 = load_rho(r1 + c1),
-          e21 = load_rho(r1 + c2);
-    float e02 = load_rho(r2 + c0), e12 = load_rho(r2 + c1);
-    float gx00 = __fmul_rn(__fsub_rn(e10, em0), 0.5f), gx10 = __fmul_rn(__fsub_rn(e20, e00), 0.5f);
-    float gx01 = __fmul_rn(__fsub_rn(e11, em1), 0.5f), gx11 = __fmul_rn(__fsub_rn(e21, e01), 0.5f);
-    float gy00 = __fmul_rn(__fsub_rn(e01, e0m), 0.5f), gy10 = __fmul_rn(__fsub_rn(e11, e1m), 0.5f);
-    float gy01 = __fmul_rn(__fsub_rn(e02, e00), 0.5f), gy11 = __fmul_rn(__fsub_rn(e12, e10), 0.5f);
-    float gx = lerp_rn(lerp_rn(gx00, gx10, fu), lerp_rn(gx01, gx11, fu), fv);
-    float gy = lerp_rn(lerp_rn(gy00, gy10, fu), lerp_rn(gy01, gy11, fu), fv);
-    float rho0 = lerp_rn(lerp_rn(e00, e10, fu), lerp_rn(e01, e11, fu), fv);
+    Frame f = frame_of(p.x, p.y, W, H);
+    const int64_t Wq = W + kQuadPad;
+    const int64_t c = (int64_t)(f.b0 + 2) * Wq + (f.a0 + 2);
+    // quads at (a0, b0-1), (a0-1, b0), (a0+1, b0), (a0, b0+1): the 12-texel stencil
+    float4 up = load_quad(Q, c - Wq), lf = load_quad(Q, c - 1);
+    float4 rt = load_quad(Q, c + 1), dn = load_quad(Q, c + Wq);
+    // E(a0,b0) = up.z, E(a0+1,b0) = up.w, E(a0,b0+1) = dn.x, E(a0+1,b0+1) = dn.y
+    float gx00 = __fmul_rn(__fsub_rn(rt.x, lf.x), 0.5f);
+    float gx10 = __fmul_rn(__fsub_rn(rt.y, lf.y), 0.5f);
+    float gx01 = __fmul_rn(__fsub_rn(rt.z, lf.z), 0.5f);
+    float gx11 = __fmul_rn(__fsub_rn(rt.w, lf.w), 0.5f);
+    float gy00 = __fmul_rn(__fsub_rn(dn.x, up.x), 0.5f);
+    float gy10 = __fmul_rn(__fsub_rn(dn.y, up.y), 0.5f);
+    float gy01 = __fmul_rn(__fsub_rn(dn.z, up.z), 0.5f);
+    float gy11 = __fmul_rn(__fsub_rn(dn.w, up.w), 0.5f);
+    float gx = lerp_rn(lerp_rn(gx00, gx10, f.fu), lerp_rn(gx01, gx11, f.fu), f.fv);
+    float gy = lerp_rn(lerp_rn(gy00, gy10, f.fu), lerp_rn(gy01, gy11, f.fu), f.fv);
+    float rho0 = lerp_rn(lerp_rn(up.z, up.w, f.fu), lerp_rn(dn.x, dn.y, f.fu), f.fv);
     float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
     float den = fmaxf(nrm, eps);
     float dx = __fdiv_rn(gx, den), dy = __fdiv_rn(gy, den);
@@ -93,7 +102,7 @@ __device__ float2 advect_point(float2 p, const T* __restrict__ L, int W, int H, 
     for (int t = 0; t < tries; ++t) {
         float xn = clamp_pos(__fmaf_rn(m, dx, p.x), W);
         float yn = clamp_pos(__fmaf_rn(m, dy, p.y), H);
-        if (density_at(L, W, H, xn, yn) >= rho0) return make_float2(xn, yn);
+        if (density_at(Q, W, H, xn, yn) >= rho0) return make_float2(xn, yn);
         m = __fmul_rn(m, 0.5f);
     }
     return p;
@@ -143,16 +152,27 @@ __device__ void block_scan_excl(const int* in, int* out, int n, int* warp_tot) {
     __syncthreads();
 }
 
-// Largest i in [lo, hi) with arr[i] <= key (arr strictly increasing on [lo, hi)).
-__device__ __forceinline__ int find_slot(const int* arr, int lo, int hi, int key) {
-    hi -= 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (arr[mid] <= key) lo = mid; else hi = mid - 1;
+// Inclusive warp scan of floats (Hillis-Steele order; the same order everywhere).
+__device__ __forceinline__ float warp_scan_incl(float x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = __fadd_rn(x, y);
     }
-    return lo;
+    return x;
 }
 
+constexpr int kWarps = kStepThreads / 32;
+constexpr int kRounds = kMaxCap / 32;  // lanes cover a polyline in this many rounds
+
+// One block of kEdgesPerBlock slots per CTA, staged through shared memory in
+// batches of whole polylines:
+//  1. load the batch's points (coalesced), map each point to its polyline;
+//  2. advection, one thread per point, in place (a point reads only itself);
+//  3. one warp per polyline: Laplacian smoothing (Jacobi, lanes = points),
+//     then the arc length by a warp scan and the new point count;
+//  4. offsets of the new polylines (block scan), then one warp per polyline
+//     writes its uniformly re-spaced points and splats them.
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     __shared__ int s_cnt[kEdgesPerBlock];
@@ -161,17 +181,17 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     __shared__ int s_w[kEdgesPerBlock];
     __shared__ int s_nn[kEdgesPerBlock];
     __shared__ int s_locn[kEdgesPerBlock + 1];
-    __shared__ float s_len[kEdgesPerBlock];
+    __shared__ float s_sp[kEdgesPerBlock];
     __shared__ int s_wtot[32];
     __shared__ float2 s_pts[kBatchPoints];
     __shared__ float s_cum[kBatchPoints];
-    constexpr int kPerThread = kBatchPoints / kStepThreads;
+    __shared__ unsigned char s_pe[kBatchPoints];
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t e0 = (int64_t)blockIdx.x * kEdgesPerBlock;
     const int nb = (int)min((int64_t)kEdgesPerBlock, a.E - e0);
     const int64_t region = (int64_t)blockIdx.x * kEdgesPerBlock * a.cap;
-    const size_t C = (size_t)a.W * a.H;
+    const int64_t QC = quad_elems(a.W, a.H);
 
     for (int i = tid; i < nb; i += kStepThreads) {
         s_cnt[i] = a.cnt_in[e0 + i];
@@ -196,111 +216,121 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
         const int p0 = s_loc[b0];
         const int np = s_loc[b1] - p0;
         for (int k = tid; k < np; k += kStepThreads) s_pts[k] = a.pts_in[region + p0 + k];
+        if (MODE & kModeAdvect) {
+            for (int i = b0 + warp; i < b1; i += kWarps) {
+                const int q = s_loc[i] - p0, n = s_cnt[i];
+                for (int j = lane; j < n; j += 32) s_pe[q + j] = (unsigned char)(i - b0);
+            }
+        }
         __syncthreads();
 
         if (MODE & kModeAdvect) {
-            // advection (Eq. 5 + halving step), in place: each point reads only itself
             for (int k = tid; k < np; k += kStepThreads) {
-                int i = find_slot(s_loc, b0, b1, p0 + k);
-                int j = p0 + k - s_loc[i];
+                const int i = b0 + s_pe[k];
+                const int j = p0 + k - s_loc[i];
                 if (j > 0 && j < s_cnt[i] - 1) {
-                    const T* L = static_cast<const T*>(a.rho) + (size_t)s_grp[i] * C;
-                    s_pts[k] = advect_point(s_pts[k], L, a.W, a.H, a.h, a.eps, a.tries);
+                    const T* Q = static_cast<const T*>(a.quads) + (int64_t)s_grp[i] * QC * 4;
+                    s_pts[k] = advect_point(s_pts[k], Q, a.W, a.H, a.h, a.eps, a.tries);
                 }
             }
-            __syncthreads();
-            // Laplacian smoothing (one Jacobi pass, endpoints fixed)
-            float2 keep[kPerThread];
-#pragma unroll
-            for (int q = 0; q < kPerThread; ++q) {
-                int k = tid + q * kStepThreads;
-                if (k < np) {
-                    int i = find_slot(s_loc, b0, b1, p0 + k);
-                    int j = p0 + k - s_loc[i];
-                    float2 A = s_pts[k];
-                    if (j > 0 && j < s_cnt[i] - 1) {
-                        float2 Ap = s_pts[k - 1], An = s_pts[k + 1];
-                        A.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.x, An.x),
-                                        __fmul_rn(a.lap_keep, A.x));
-                        A.y = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.y, An.y),
-                                        __fmul_rn(a.lap_keep, A.y));
-                    }
-                    keep[q] = A;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < kPerThread; ++q) {
-                int k = tid + q * kStepThreads;
-                if (k < np) {
-                    s_pts[k] = keep[q];
-                    if (!(MODE & kModeResample)) a.pts_out[region + p0 + k] = keep[q];
-                }
-            }
-            if (!(MODE & kModeResample))
-                for (int i = b0 + tid; i < b1; i += kStepThreads) a.cnt_out[e0 + i] = s_cnt[i];
             __syncthreads();
         }
 
-        if (MODE & kModeResample) {
-            // arc length by sequential summation from the source, one thread per polyline
-            for (int i = b0 + tid; i < b1; i += kStepThreads) {
-                int q = s_loc[i] - p0, n = s_cnt[i];
-                float c = 0.0f;
-                s_cum[q] = 0.0f;
-                for (int s = 1; s < n; ++s) {
-                    c = __fadd_rn(c, seg_len(s_pts[q + s - 1], s_pts[q + s]));
-                    s_cum[q + s] = c;
+        // one warp per polyline: Laplacian, then arc length and new count
+        for (int i = b0 + warp; i < b1; i += kWarps) {
+            const int q = s_loc[i] - p0, n = s_cnt[i];
+            if (MODE & kModeAdvect) {
+                float2 P[kRounds];
+#pragma unroll
+                for (int r = 0; r < kRounds; ++r) {
+                    const int j = lane + 32 * r;
+                    if (j < n) {
+                        float2 A = s_pts[q + j];
+                        if (j > 0 && j < n - 1) {
+                            float2 Ap = s_pts[q + j - 1], An = s_pts[q + j + 1];
+                            A.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.x, An.x),
+                                            __fmul_rn(a.lap_keep, A.x));
+                            A.y = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.y, An.y),
+                                            __fmul_rn(a.lap_keep, A.y));
+                        }
+                        P[r] = A;
+                    }
                 }
-                s_len[i] = c;
-                s_nn[i] = new_count(c, a);
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < kRounds; ++r) {
+                    const int j = lane + 32 * r;
+                    if (j < n) {
+                        s_pts[q + j] = P[r];
+                        if (!(MODE & kModeResample)) a.pts_out[region + p0 + q + j] = P[r];
+                    }
+                }
+                if (!(MODE & kModeResample) && lane == 0) a.cnt_out[e0 + i] = n;
+                __syncwarp();
             }
-            __syncthreads();
+            if (MODE & kModeResample) {
+                float carry = 0.0f;
+#pragma unroll
+                for (int r = 0; r < kRounds; ++r) {
+                    const int j = lane + 32 * r;
+                    float sl = 0.0f;
+                    if (j >= 1 && j < n) sl = seg_len(s_pts[q + j - 1], s_pts[q + j]);
+                    float c = __fadd_rn(warp_scan_incl(sl, lane), carry);
+                    if (j < n) s_cum[q + j] = c;
+                    carry = __shfl_sync(0xffffffffu, c, 31);
+                }
+                if (lane == 0) {
+                    const int m = new_count(carry, a);
+                    s_nn[i] = m;
+                    s_sp[i] = __fdiv_rn(carry, (float)(m - 1));
+                }
+            }
+        }
+        __syncthreads();
+
+        if (MODE & kModeResample) {
             block_scan_excl(s_nn + b0, s_locn + b0, b1 - b0, s_wtot);
-            const int nout = s_locn[b1];
-            // one thread per output point: uniform arc-length positions
-            for (int o = tid; o < nout; o += kStepThreads) {
-                int i = find_slot(s_locn, b0, b1, o);
-                int j = o - s_locn[i];
-                int m = s_nn[i];
-                int q = s_loc[i] - p0, n = s_cnt[i];
-                float2 R;
-                if (j == 0) {
-                    R = s_pts[q];
-                } else if (j == m - 1) {
-                    R = s_pts[q + n - 1];
-                } else {
-                    float L = s_len[i];
-                    if (L == 0.0f) {
+            for (int i = b0 + warp; i < b1; i += kWarps) {
+                const int q = s_loc[i] - p0, n = s_cnt[i], m = s_nn[i];
+                const float sp = s_sp[i];
+                const bool flat = s_cum[q + n - 1] == 0.0f;
+                const int64_t ob = region + out_base + s_locn[i];
+                const int g = s_grp[i], w = s_w[i];
+                uint32_t* hl = a.hist + (size_t)g * a.W * a.H;
+                for (int j = lane; j < m; j += 32) {
+                    float2 R;
+                    if (j == m - 1) {
+                        R = s_pts[q + n - 1];
+                    } else if (j == 0 || flat) {
                         R = s_pts[q];
                     } else {
-                        float t = __fdiv_rn(__fmul_rn((float)j, L), (float)(m - 1));
+                        // point j sits at arc length j * L / (m - 1) on the polyline
+                        const float t = __fmul_rn((float)j, sp);
                         int lo = 1, hi = n - 1;
                         while (lo < hi) {
                             int mid = (lo + hi) >> 1;
                             if (s_cum[q + mid] > t) hi = mid; else lo = mid + 1;
                         }
-                        float c0 = s_cum[q + lo - 1];
-                        float seg = __fsub_rn(s_cum[q + lo], c0);
-                        float f = seg > 0.0f ? __fdiv_rn(__fsub_rn(t, c0), seg) : 0.0f;
-                        f = fminf(fmaxf(f, 0.0f), 1.0f);
-                        float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
-                        R = make_float2(lerp_rn(A.x, B.x, f), lerp_rn(A.y, B.y, f));
+                        const float c0 = s_cum[q + lo - 1];
+                        const float seg = __fsub_rn(s_cum[q + lo], c0);
+                        float fr = seg > 0.0f ? __fdiv_rn(__fsub_rn(t, c0), seg) : 0.0f;
+                        fr = fminf(fmaxf(fr, 0.0f), 1.0f);
+                        const float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
+                        R = make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr));
+                    }
+                    a.pts_out[ob + j] = R;
+                    // splat: the point adds its edge weight to its group's cell (Eq. 1, Eq. 3)
+                    if (w != 0) {
+                        const int cx = min(max((int)floorf(R.x), 0), a.W - 1);
+                        const int cy = min(max((int)floorf(R.y), 0), a.H - 1);
+                        atomicAdd(hl + (size_t)cy * a.W + cx, (unsigned)w);
                     }
                 }
-                a.pts_out[region + out_base + o] = R;
-                // splat: the point adds its edge weight to its group's cell (Eq. 1, Eq. 3)
-                int w = s_w[i];
-                if (w != 0) {
-                    int cx = min(max((int)floorf(R.x), 0), a.W - 1);
-                    int cy = min(max((int)floorf(R.y), 0), a.H - 1);
-                    atomicAdd(a.hist + (size_t)s_grp[i] * C + (size_t)cy * a.W + cx,
-                              (unsigned)w);
-                }
+                if (lane == 0) a.cnt_out[e0 + i] = m;
             }
-            for (int i = b0 + tid; i < b1; i += kStepThreads) a.cnt_out[e0 + i] = s_nn[i];
-            if (tid == 0 && a.n_splat) atomicAdd(a.n_splat, (unsigned long long)nout);
-            out_base += nout;
+            if (tid == 0 && a.n_splat)
+                atomicAdd(a.n_splat, (unsigned long long)s_locn[b1]);
+            out_base += s_locn[b1];
             __syncthreads();
         }
         b0 = b1;
