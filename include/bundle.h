@@ -189,6 +189,34 @@ bundle_status bundle_profile_enable(bundle_ctx* ctx, int32_t on);
 bundle_status bundle_profile_read(bundle_ctx* ctx, double* ms, int64_t* launches, int32_t n,
                                   int32_t reset);
 
+/*
+ * Box-pass smoothing that allocates no memory (the paper has no counterpart;
+ * it is an integration aid). Some callers cannot call cudaMalloc: code running
+ * under a framework whose caching allocator owns all device memory, services
+ * that reserve their memory budget up front, or paths that must avoid the
+ * implicit synchronisation cudaMalloc/cudaFree can cause. This entry point
+ * runs the same row and column box passes as bundle_iterate with its
+ * intermediate stack in a fixed 16 MiB device array compiled into the library
+ * (every GPU that loads the library holds it until exit).
+ *  hist: device uint32 [n_groups][grid_h][grid_w] histogram (input).
+ *  sums: device [n_groups][grid_h][grid_w] int32 (sum_bits 32) or int64
+ *        (sum_bits 64) output: `passes` unnormalised (2r+1)^2 box sums with
+ *        half-sample reflection, exactly as BUNDLE_DENSITY_SUMS.
+ *  sum_bits must hold 4 (2r+1)^(2(passes-1)) times the histogram's total; the
+ *  call does not check this bound (bundle_init does, for its own contexts).
+ *  stream: cudaStream_t, NULL for the legacy default stream; asynchronous.
+ * Returns EINVAL when n_groups * grid_h * grid_w * sum_bits / 8 exceeds
+ * 16 MiB or an argument is out of range (message via bundle_last_error(NULL)),
+ * ECUDA on a launch failure. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the one array and it keeps the last call's
+ * contents; nothing in it needs clearing (the row passes overwrite every cell
+ * the column passes read), but calls that overlap on the GPU race on it.
+ */
+bundle_status bundle_smooth_noalloc(const uint32_t* hist, void* sums, int32_t n_groups,
+                                    int32_t grid_h, int32_t grid_w, int32_t radius,
+                                    int32_t passes, int32_t sum_bits, void* stream);
+
 /* Wait for the context's stream; reports a deferred kernel error as ECUDA. */
 bundle_status bundle_sync(bundle_ctx* ctx);
 

@@ -32,7 +32,7 @@ PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "c
 EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bundle_iterate",
             "bundle_fetch", "bundle_fetch_density", "bundle_get_info", "bundle_sync",
             "bundle_destroy", "bundle_last_error", "bundle_status_string",
-            "bundle_profile_enable", "bundle_profile_read")
+            "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc")
 
 
 class BundleParams(ctypes.Structure):
@@ -109,6 +109,8 @@ def lib():
     L.bundle_profile_enable.restype = i32
     L.bundle_profile_read.argtypes = [P, P, P, i32, i32]
     L.bundle_profile_read.restype = i32
+    L.bundle_smooth_noalloc.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P]
+    L.bundle_smooth_noalloc.restype = i32
     _lib = L
     return L
 
@@ -259,6 +261,18 @@ def bundle_profile_read(ctx, reset: bool = True) -> dict:
     cnt = np.zeros(n, np.int64)
     _check(lib().bundle_profile_read(ctx, _ptr(ms), _ptr(cnt), n, 1 if reset else 0), ctx)
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def bundle_smooth_noalloc(hist, sums, radius: int, passes: int, stream=None):
+    """Box-pass smoothing of a device histogram into a caller-provided device output, with no
+    allocation by the library (for callers that cannot allocate device memory themselves:
+    see include/bundle.h). hist: CUDA uint32/int32 tensor [G, H, W]; sums: CUDA int32 or
+    int64 tensor [G, H, W] (its dtype picks the sum width)."""
+    G, H, W = (int(x) for x in hist.shape)
+    bits = 8 * sums.element_size()
+    _check(lib().bundle_smooth_noalloc(_ptr(hist), _ptr(sums), G, H, W, int(radius),
+                                       int(passes), bits, _stream_handle(stream)))
+    return sums
 
 
 def bundle_destroy(ctx):

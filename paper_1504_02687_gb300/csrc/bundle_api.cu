@@ -63,6 +63,12 @@ namespace {
 
 thread_local std::string g_init_error;
 
+}  // namespace
+
+void heb::set_thread_error(const char* msg) { g_init_error = msg; }
+
+namespace {
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {

@@ -107,4 +107,7 @@ cudaError_t launch_sum_counts(const int32_t* cnt, int64_t E, unsigned long long*
                               cudaStream_t st);
 size_t scan_offsets_tmp_elems(int64_t E);
 
+// Message returned by bundle_last_error(NULL) on this thread.
+void set_thread_error(const char* msg);
+
 }  // namespace heb
