@@ -143,7 +143,7 @@ def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho):
     if kind == "advect":
         return 16 * N + 12 * E + GC * b_rho
     if kind == "rowbox":
-        return GC * (4 + b_sum)
+        return GC * (4 + b_sum)  # the histogram once (its copies are workspace) + the output
     if kind == "colbox":
         return 2 * GC * b_sum
     if kind == "combine":

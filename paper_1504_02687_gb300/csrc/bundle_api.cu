@@ -311,7 +311,7 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
         CUDA_TRY(e, dalloc(c, &c->cnt[b], E));
         CUDA_TRY(e, dalloc(c, &c->pts[b], region));
     }
-    CUDA_TRY(e, dalloc(c, &c->hist, C));
+    CUDA_TRY(e, dalloc(c, &c->hist, C * kHistCopies));
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->Y), C * sb));
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->S), C * sb));
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->rho), C * rho_bytes(c->p.rho_dtype)));
@@ -320,7 +320,7 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     CUDA_TRY(e, dalloc(c, &c->counters, 4));
     CUDA_TRY(e, dalloc(c, &c->fetch_off, (size_t)E + 1));
     CUDA_TRY(e, dalloc(c, &c->fetch_tmp, scan_offsets_tmp_elems(E) + 1));
-    CUDA_TRY(e, cudaMemsetAsync(c->hist, 0, C * sizeof(uint32_t), c->stream));
+    CUDA_TRY(e, cudaMemsetAsync(c->hist, 0, C * kHistCopies * sizeof(uint32_t), c->stream));
     CUDA_TRY(e, cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream));
     return BUNDLE_OK;
 }
@@ -457,6 +457,7 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
     a.cap = c->cap;
     a.W = c->W;
     a.H = c->H;
+    a.G = c->G;
     a.h = h;
     a.eps = c->p.eps;
     a.tries = c->p.step_tries;
@@ -468,7 +469,7 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
     if (mode & kModeResample)
         CUDA_TRY(&c->err, timed(c, kProfHistClear, [&] {
                      return cudaMemsetAsync(c->hist, 0,
-                                            (size_t)c->G * c->H * c->W * sizeof(uint32_t),
+                                            (size_t)kHistCopies * c->G * c->H * c->W * sizeof(uint32_t),
                                             c->stream);
                  }));
     const int kind = mode == kModeResample ? kProfResample
@@ -480,6 +481,7 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
 bundle_status run_filter(bundle_ctx* c) {
     FilterArgs f{};
     f.hist = c->hist;
+    f.hist_copies = kHistCopies;
     f.Y = c->Y;
     f.S = c->S;
     f.rho = c->rho;
@@ -828,6 +830,8 @@ bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int6
         return fail(&c->err, BUNDLE_EINVAL, "dst holds %lld bytes, %zu needed",
                     (long long)dst_bytes, bytes);
     DeviceGuard dg(c->device);
+    if (which == BUNDLE_DENSITY_HIST)
+        CUDA_TRY(&c->err, launch_fold_hist(c->hist, (int64_t)C, kHistCopies, c->stream));
     CUDA_TRY(&c->err, cudaMemcpyAsync(dst, src, bytes,
                                       (flags & BUNDLE_FETCH_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                     : cudaMemcpyDeviceToHost,

@@ -16,9 +16,14 @@ namespace heb {
 // counts are stored: a block recovers its edges' offsets with one scan.
 constexpr int kEdgesPerBlock = 128;
 constexpr int kStepThreads = 256;
-constexpr int kBatchPoints = 3072;  // points staged in shared memory per batch
+constexpr int kBatchPoints = 2048;  // points staged in shared memory per batch
 constexpr int kMaxCap = 64;         // largest polyline (n_fixed or n_max): two warp rounds
 constexpr float kEdgeGuard = 0.0009765625f;  // positions stay below W - 2^-10
+// The splat writes into kHistCopies copies of the histogram (block b into copy
+// b mod kHistCopies) and the row-pass kernel sums them as it reads: bundled
+// polylines put many points on the same cells, and atomics on one address
+// serialise in L2, so spreading them over copies shortens those queues.
+constexpr int kHistCopies = 2;
 
 enum StepMode : int {
     kModeResample = 2,                // resample + splat the input polylines
@@ -38,7 +43,7 @@ struct StepArgs {
     unsigned long long* n_splat;  // running count of splatted points
     int64_t E;
     int32_t cap;             // points per slot of the region (n_fixed or n_max)
-    int32_t W, H;
+    int32_t W, H, G;
     float h;                 // step magnitude h_i
     float eps;               // Eq. 5 epsilon
     int32_t tries;           // step sizes tried
@@ -49,7 +54,8 @@ struct StepArgs {
 };
 
 struct FilterArgs {
-    const uint32_t* hist;  // [G][H][W]
+    const uint32_t* hist;  // [copies][G][H][W]: the histogram is the sum of the copies
+    int32_t hist_copies;
     void* Y;               // [G][H][W] row-filtered workspace (sum type)
     void* S;               // [G][H][W] smoothed sums (sum type)
     void* rho;             // [G][H][W] density (rho type)
@@ -79,6 +85,8 @@ cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st);
+// Fold histogram copies 1.. into copy 0 (their sum is unchanged), n cells per copy.
+cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t st);
 
 // Init / fetch helpers (point layout <-> caller order).
 cudaError_t launch_edge_keys(const float2* src, const float2* dst, const int32_t* group,

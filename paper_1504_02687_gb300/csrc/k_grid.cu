@@ -23,8 +23,8 @@ __device__ __forceinline__ int reflect_index(int i, int n) {
 // [l*c, (l+1)*c) of the row; the shared row is padded after every chunk so the
 // 32 lanes walking their chunks in lockstep hit distinct banks.
 template <typename TS>
-__global__ void k_rowbox(const uint32_t* __restrict__ hist, TS* __restrict__ Y, int G, int H,
-                         int W, int r, int passes, int rows, int c, int pad) {
+__global__ void k_rowbox(const uint32_t* __restrict__ hist, int copies, TS* __restrict__ Y, int G,
+                         int H, int W, int r, int passes, int rows, int c, int pad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.y;
@@ -34,7 +34,32 @@ __global__ void k_rowbox(const uint32_t* __restrict__ hist, TS* __restrict__ Y, 
     TS* src = reinterpret_cast<TS*>(smem_raw) + (size_t)warp * 2 * stride;
     TS* dst = src + stride;
     const size_t base = ((size_t)g * H + v) * W;
-    for (int x = lane; x < W; x += 32) src[x + (x / c) * pad] = (TS)hist[base + x];
+    const size_t stride_copy = (size_t)G * H * W;
+    if ((W & 3) == 0) {
+        // 16-byte loads of every copy, all issued before they are summed
+        const uint4* h0 = reinterpret_cast<const uint4*>(hist + base);
+        for (int x4 = lane; x4 < (W >> 2); x4 += 32) {
+            uint4 v = __ldg(h0 + x4);
+            for (int k = 1; k < copies; ++k) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4*>(hist + k * stride_copy + base) + x4);
+                v.x += u.x;
+                v.y += u.y;
+                v.z += u.z;
+                v.w += u.w;
+            }
+            const int x = 4 * x4;
+            src[x + (x / c) * pad] = (TS)v.x;
+            src[x + 1 + ((x + 1) / c) * pad] = (TS)v.y;
+            src[x + 2 + ((x + 2) / c) * pad] = (TS)v.z;
+            src[x + 3 + ((x + 3) / c) * pad] = (TS)v.w;
+        }
+    } else {
+        for (int x = lane; x < W; x += 32) {
+            TS v = (TS)hist[base + x];
+            for (int k = 1; k < copies; ++k) v += (TS)hist[k * stride_copy + base + x];
+            src[x + (x / c) * pad] = v;
+        }
+    }
     __syncwarp();
     const int i0 = lane * c, i1 = min(i0 + c, W);
     for (int p = 0; p < passes; ++p) {
@@ -199,8 +224,9 @@ cudaError_t rowbox_t(const FilterArgs& a, cudaStream_t st) {
                                            (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)((a.H + rows - 1) / rows), (unsigned)a.G);
-    kern<<<grid, 32 * rows, smem, st>>>(a.hist, static_cast<TS*>(a.Y), a.G, a.H, a.W, a.r,
-                                        a.passes, rows, c, pad);
+    kern<<<grid, 32 * rows, smem, st>>>(a.hist, a.hist_copies < 1 ? 1 : a.hist_copies,
+                                        static_cast<TS*>(a.Y), a.G, a.H, a.W, a.r, a.passes,
+                                        rows, c, pad);
     return cudaGetLastError();
 }
 
@@ -243,6 +269,23 @@ cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
 
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
     return sum_bits == 32 ? colbox_t<uint32_t>(a, st) : colbox_t<unsigned long long>(a, st);
+}
+
+__global__ void k_fold_hist(uint32_t* hist, int64_t n, int copies) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t v = hist[i];
+    for (int k = 1; k < copies; ++k) {
+        v += hist[k * n + i];
+        hist[k * n + i] = 0;
+    }
+    hist[i] = v;
+}
+
+cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t st) {
+    if (copies <= 1 || n <= 0) return cudaSuccess;
+    k_fold_hist<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(hist, n, copies);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st) {

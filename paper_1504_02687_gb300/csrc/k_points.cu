@@ -95,9 +95,10 @@ __device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, 
     float gx = lerp_rn(lerp_rn(gx00, gx10, f.fu), lerp_rn(gx01, gx11, f.fu), f.fv);
     float gy = lerp_rn(lerp_rn(gy00, gy10, f.fu), lerp_rn(gy01, gy11, f.fu), f.fv);
     float rho0 = lerp_rn(lerp_rn(up.z, up.w, f.fu), lerp_rn(dn.x, dn.y, f.fu), f.fv);
-    float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
-    float den = fmaxf(nrm, eps);
-    float dx = __fdiv_rn(gx, den), dy = __fdiv_rn(gy, den);
+    // d = g / max(|g|, eps): one reciprocal square root (direction only)
+    const float n2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+    const float inv = n2 > eps * eps ? rsqrtf(n2) : __frcp_rn(eps);
+    const float dx = __fmul_rn(gx, inv), dy = __fmul_rn(gy, inv);
     float m = h;
     for (int t = 0; t < tries; ++t) {
         float xn = clamp_pos(__fmaf_rn(m, dx, p.x), W);
@@ -108,9 +109,11 @@ __device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, 
     return p;
 }
 
+// Segment length (the arc length sums these; an approximate square root is enough).
 __device__ __forceinline__ float seg_len(float2 a, float2 b) {
     float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y);
-    return __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+    float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return d2 > 0.0f ? __fmul_rn(d2, rsqrtf(d2)) : 0.0f;
 }
 
 // Point count after resampling (Sec. 2.1: spacing delta; fixed count if set).
@@ -163,6 +166,18 @@ __device__ __forceinline__ float warp_scan_incl(float x, int lane) {
 }
 
 constexpr int kWarps = kStepThreads / 32;
+
+// Write one resampled point and splat it: it adds its edge weight to its group's cell
+// (Eq. 1, Eq. 3) in one of the histogram copies.
+__device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at, float2 R,
+                                     int w) {
+    a.pts_out[at] = R;
+    if (w != 0) {
+        const int cx = min(max((int)floorf(R.x), 0), a.W - 1);
+        const int cy = min(max((int)floorf(R.y), 0), a.H - 1);
+        atomicAdd(hl + (size_t)cy * a.W + cx, (unsigned)w);
+    }
+}
 constexpr int kRounds = kMaxCap / 32;  // lanes cover a polyline in this many rounds
 
 // One block of kEdgesPerBlock slots per CTA, staged through shared memory in
@@ -192,6 +207,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     const int nb = (int)min((int64_t)kEdgesPerBlock, a.E - e0);
     const int64_t region = (int64_t)blockIdx.x * kEdgesPerBlock * a.cap;
     const int64_t QC = quad_elems(a.W, a.H);
+    const size_t hist_copy = blockIdx.x % kHistCopies;
 
     for (int i = tid; i < nb; i += kStepThreads) {
         s_cnt[i] = a.cnt_in[e0 + i];
@@ -270,8 +286,10 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
             }
             if (MODE & kModeResample) {
                 float carry = 0.0f;
+                const int rounds = (n + 31) >> 5;
 #pragma unroll
                 for (int r = 0; r < kRounds; ++r) {
+                    if (r >= rounds) break;
                     const int j = lane + 32 * r;
                     float sl = 0.0f;
                     if (j >= 1 && j < n) sl = seg_len(s_pts[q + j - 1], s_pts[q + j]);
@@ -293,37 +311,32 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
             for (int i = b0 + warp; i < b1; i += kWarps) {
                 const int q = s_loc[i] - p0, n = s_cnt[i], m = s_nn[i];
                 const float sp = s_sp[i];
-                const bool flat = s_cum[q + n - 1] == 0.0f;
+                const float L = s_cum[q + n - 1];
                 const int64_t ob = region + out_base + s_locn[i];
                 const int g = s_grp[i], w = s_w[i];
-                uint32_t* hl = a.hist + (size_t)g * a.W * a.H;
+                uint32_t* hl = a.hist + hist_copy * a.G * (size_t)a.W * a.H + (size_t)g * a.W * a.H;
+                // endpoints are copied; an edge of zero length puts every point on its source
                 for (int j = lane; j < m; j += 32) {
-                    float2 R;
-                    if (j == m - 1) {
-                        R = s_pts[q + n - 1];
-                    } else if (j == 0 || flat) {
-                        R = s_pts[q];
-                    } else {
-                        // point j sits at arc length j * L / (m - 1) on the polyline
+                    if (j == m - 1) emit(a, hl, ob + j, s_pts[q + n - 1], w);
+                    else if (j == 0 || L == 0.0f) emit(a, hl, ob + j, s_pts[q], w);
+                }
+                if (L > 0.0f && m > 2) {
+                    // interior output j sits at arc length t_j = j * L / (m - 1) on segment s,
+                    // the first with cum[s] > t_j (binary search on the polyline's cum)
+                    for (int j = 1 + lane; j < m - 1; j += 32) {
                         const float t = __fmul_rn((float)j, sp);
                         int lo = 1, hi = n - 1;
                         while (lo < hi) {
-                            int mid = (lo + hi) >> 1;
+                            const int mid = (lo + hi) >> 1;
                             if (s_cum[q + mid] > t) hi = mid; else lo = mid + 1;
                         }
                         const float c0 = s_cum[q + lo - 1];
                         const float seg = __fsub_rn(s_cum[q + lo], c0);
-                        float fr = seg > 0.0f ? __fdiv_rn(__fsub_rn(t, c0), seg) : 0.0f;
+                        float fr = seg > 0.0f ? __fdividef(__fsub_rn(t, c0), seg) : 0.0f;
                         fr = fminf(fmaxf(fr, 0.0f), 1.0f);
                         const float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
-                        R = make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr));
-                    }
-                    a.pts_out[ob + j] = R;
-                    // splat: the point adds its edge weight to its group's cell (Eq. 1, Eq. 3)
-                    if (w != 0) {
-                        const int cx = min(max((int)floorf(R.x), 0), a.W - 1);
-                        const int cy = min(max((int)floorf(R.y), 0), a.H - 1);
-                        atomicAdd(hl + (size_t)cy * a.W + cx, (unsigned)w);
+                        emit(a, hl, ob + j,
+                             make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr)), w);
                     }
                 }
                 if (lane == 0) a.cnt_out[e0 + i] = m;

@@ -79,6 +79,7 @@ extern "C" bundle_status bundle_smooth_noalloc(const uint32_t* hist, void* sums,
     }
     heb::FilterArgs f{};
     f.hist = hist;
+    f.hist_copies = 1;
     f.Y = Y;
     f.S = sums;
     f.G = n_groups;
