@@ -255,6 +255,21 @@ def run_reference(args):
     }))
 
 
+def reduce_over_ranks(dist, ms: float, updates: float, device=None):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of the updates all
+    ranks made (independent graphs per rank, weak scaling). `device` is where the collective's
+    tensors live (CUDA for NCCL, CPU for gloo)."""
+    if dist is None:
+        return ms, updates
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -316,15 +331,7 @@ def run_ours(args):
     updates = info.points_processed - done0
     E = info.n_edges
     N_avg = updates / max(args.steps, 1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        u = torch.tensor([float(updates)], device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_updates = float(u.item())
-    else:
-        total_updates = float(updates)
+    ms, total_updates = reduce_over_ranks(dist, ms, float(updates), device="cuda")
     value = total_updates / (ms / 1e3)
 
     kern = {k: v for k, v in prof.items() if v[1] > 0}
@@ -406,14 +413,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         upd3 = inf3.points_processed
         pkg.bundle_destroy(c3)
-        e2e_s = t1 - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-            u = torch.tensor([float(upd3)], device="cuda")
-            dist.all_reduce(u, op=dist.ReduceOp.SUM)
-            upd3 = u.item()
+        e2e_s, upd3 = reduce_over_ranks(dist, t1 - t0, float(upd3), device="cuda")
         h2d = w.n_edges * (8 + 8 + 4)
         d2h = (E + 1) * 8 + int(inf3.n_points) * 8
         out["e2e"] = {"value": upd3 / e2e_s, "unit": UNIT,
