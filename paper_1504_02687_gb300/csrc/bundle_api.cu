@@ -22,6 +22,7 @@ struct bundle_ctx {
     int64_t E = 0;
     int32_t G = 1, W = 0, H = 0;
     int32_t cap = 0;
+    int32_t eb = kEdgesPerBlock;  // edges per block of the point layout
     int64_t n_blocks = 0;
     int32_t sum_bits = 64;
     int64_t mix_self = 1, mix_all = 0;
@@ -51,6 +52,14 @@ struct bundle_ctx {
     int cur_R = -1;      // buffer holding the last resampled polylines (-1: none yet)
     bool have_density = false;
     int64_t device_bytes = 0;
+    // device schedule of h and the graphs of one steady-state iteration (one per ping-pong
+    // direction); launched instead of separate kernels when profiling is off
+    float* h_sched = nullptr;
+    int32_t h_cap = 0;
+    int32_t* d_iter = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool use_graphs = true;
     // per-kernel event timing (bundle_profile_enable)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -121,6 +130,11 @@ void free_ctx(bundle_ctx* c) {
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    for (cudaGraphExec_t g : c->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->h_sched) cudaFree(c->h_sched);
+    if (c->d_iter) cudaFree(c->d_iter);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -300,8 +314,13 @@ bundle_status grid_map(bundle_ctx* c, const float* src, const float* dst, std::s
 // Device buffers sized from E, cap, G, H, W and the widths.
 bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     const int64_t E = c->E;
-    c->n_blocks = (E + kEdgesPerBlock - 1) / kEdgesPerBlock;
-    const size_t region = (size_t)c->n_blocks * kEdgesPerBlock * c->cap;
+    // blocks of up to 128 edges; small graphs use smaller blocks so that at least ~4 CTAs
+    // per SM (152 SMs) have work
+    int eb = kEdgesPerBlock;
+    while (eb > 8 && E < (int64_t)eb * 152 * 4) eb /= 2;
+    c->eb = eb;
+    c->n_blocks = (E + eb - 1) / eb;
+    const size_t region = (size_t)c->n_blocks * eb * c->cap;
     const size_t C = (size_t)c->G * c->H * c->W;
     const size_t sb = c->sum_bits / 8;
     CUDA_TRY(e, dalloc(c, &c->perm, E));
@@ -318,6 +337,7 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->quads),
                        (size_t)c->G * quad_elems(c->W, c->H) * 4 * rho_bytes(c->p.rho_dtype)));
     CUDA_TRY(e, dalloc(c, &c->counters, 4));
+    CUDA_TRY(e, dalloc(c, &c->d_iter, 1));
     CUDA_TRY(e, dalloc(c, &c->fetch_off, (size_t)E + 1));
     CUDA_TRY(e, dalloc(c, &c->fetch_tmp, scan_offsets_tmp_elems(E) + 1));
     CUDA_TRY(e, cudaMemsetAsync(c->hist, 0, C * kHistCopies * sizeof(uint32_t), c->stream));
@@ -442,7 +462,7 @@ cudaError_t timed(bundle_ctx* c, int kind, F fn) {
     return e;
 }
 
-bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
+bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
     StepArgs a{};
     a.cnt_in = c->cnt[in];
     a.pts_in = c->pts[in];
@@ -454,11 +474,14 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out, float h) {
     a.hist = c->hist;
     a.n_splat = c->counters;
     a.E = c->E;
+    a.eb = c->eb;
     a.cap = c->cap;
     a.W = c->W;
     a.H = c->H;
     a.G = c->G;
-    a.h = h;
+    a.h = 0.0f;
+    a.h_sched = c->h_sched;
+    a.iter = c->d_iter;
     a.eps = c->p.eps;
     a.tries = c->p.step_tries;
     a.lap_keep = (float)(1.0 - (double)c->p.laplace_beta);
@@ -500,6 +523,78 @@ bundle_status run_filter(bundle_ctx* c) {
                  return launch_combine(c->sum_bits, c->p.rho_dtype, f, c->stream);
              }));
     CUDA_TRY(&c->err, timed(c, kProfQuads, [&] { return launch_quads(c->p.rho_dtype, f, c->stream); }));
+    return BUNDLE_OK;
+}
+
+// The device schedule holds h_i for i < h_cap, filled by the same repeated
+// multiplication as bandwidth(); it grows (doubling) when iterations run past it.
+bundle_status ensure_schedule(bundle_ctx* c, int32_t needed) {
+    if (needed <= c->h_cap && c->h_sched) return BUNDLE_OK;
+    int32_t cap = c->h_cap > 0 ? c->h_cap : 1024;
+    while (cap < needed) cap *= 2;
+    std::vector<float> tab((size_t)cap);
+    double h = bandwidth(c->p, 0);
+    for (int32_t i = 0; i < cap; ++i) {
+        tab[(size_t)i] = (float)h;
+        h *= c->p.lambda;
+    }
+    float* d = nullptr;
+    CUDA_TRY(&c->err, cudaMalloc(&d, (size_t)cap * sizeof(float)));
+    cudaError_t e = cudaMemcpy(d, tab.data(), (size_t)cap * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        CUDA_TRY(&c->err, e);
+    }
+    if (c->h_sched) {
+        CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+        cudaFree(c->h_sched);
+        c->device_bytes -= (int64_t)c->h_cap * 4;
+    }
+    c->h_sched = d;
+    c->device_bytes += (int64_t)cap * 4;
+    c->h_cap = cap;
+    for (cudaGraphExec_t& g : c->gexec)  // the graphs hold the old pointer
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return BUNDLE_OK;
+}
+
+// One steady-state iteration: layer filter, mix, quads, histogram clear, the fused
+// advect -> resample -> splat step from buffer R to 1 - R, then the counter advance.
+bundle_status launch_iteration(bundle_ctx* c, int R) {
+    bundle_status s = run_filter(c);
+    if (s != BUNDLE_OK) return s;
+    s = run_step(c, kModeAdvectResample, R, 1 - R);
+    if (s != BUNDLE_OK) return s;
+    CUDA_TRY(&c->err, launch_advance_iter(c->d_iter, c->stream));
+    return BUNDLE_OK;
+}
+
+bundle_status build_graph(bundle_ctx* c, int R) {
+    if (!c->cap_stream)
+        CUDA_TRY(&c->err, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    bundle_status s = e == cudaSuccess ? launch_iteration(c, R) : BUNDLE_ECUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    c->stream = saved;
+    if (e != cudaSuccess) return fail(&c->err, BUNDLE_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    if (s != BUNDLE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e2 != cudaSuccess)
+        return fail(&c->err, BUNDLE_ECUDA, "graph capture end: %s", cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&c->gexec[R], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[R] = nullptr;
+        return fail(&c->err, BUNDLE_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
     return BUNDLE_OK;
 }
 
@@ -589,7 +684,7 @@ bundle_status bundle_init(bundle_ctx** out, const bundle_params* p, int64_t n_ed
     bundle_status st = BUNDLE_OK;
     if (err == cudaSuccess) st = sort_edges(c, d_src, d_dst, d_g, d_w, e);
     if (err == cudaSuccess && st == BUNDLE_OK)
-        err = launch_straight_layout(c->perm, n_edges, d_src, d_dst, c->cap, c->cnt[0],
+        err = launch_straight_layout(c->perm, n_edges, d_src, d_dst, c->eb, c->cap, c->cnt[0],
                                      c->pts[0], c->stream);
     if (err == cudaSuccess && st == BUNDLE_OK) err = cudaStreamSynchronize(c->stream);
     cudaFree(d_src);
@@ -696,8 +791,8 @@ bundle_status bundle_init_polylines(bundle_ctx** out, const bundle_params* p, in
     bundle_status st = BUNDLE_OK;
     if (err == cudaSuccess) st = sort_edges(c, d_src, d_dst, d_g, d_w, e);
     if (err == cudaSuccess && st == BUNDLE_OK)
-        err = launch_polyline_layout(c->perm, n_edges, d_off, d_xy, c->cap, c->cnt[0], c->pts[0],
-                                     c->stream);
+        err = launch_polyline_layout(c->perm, n_edges, d_off, d_xy, c->eb, c->cap, c->cnt[0],
+                                     c->pts[0], c->stream);
     if (err == cudaSuccess && st == BUNDLE_OK) err = cudaStreamSynchronize(c->stream);
     cudaFree(d_src);
     cudaFree(d_dst);
@@ -720,25 +815,32 @@ bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
     if (n_iters < 0) return fail(&c->err, BUNDLE_EINVAL, "n_iters must be >= 0");
     if (n_iters == 0) return BUNDLE_OK;
     DeviceGuard dg(c->device);
+    bundle_status s = ensure_schedule(c, c->iteration + n_iters);
+    if (s != BUNDLE_OK) return s;
+    CUDA_TRY(&c->err, launch_set_iter(c->d_iter, c->iteration, c->stream));
     // resample the current polylines and splat them (start of the first iteration)
     int src = c->cur_P, dst = 1 - c->cur_P;
-    bundle_status s = run_step(c, kModeResample, src, dst, 0.0f);
+    s = run_step(c, kModeResample, src, dst);
     if (s != BUNDLE_OK) return s;
     int R = dst;
     for (int32_t it = 0; it < n_iters; ++it) {
-        s = run_filter(c);
-        if (s != BUNDLE_OK) return s;
-        float h = (float)bandwidth(c->p, c->iteration);
-        bool last = it == n_iters - 1;
-        s = run_step(c, last ? kModeAdvect : kModeAdvectResample, R, 1 - R, h);
-        if (s != BUNDLE_OK) return s;
-        c->iteration += 1;
+        const bool last = it == n_iters - 1;
         if (last) {
+            s = run_filter(c);
+            if (s == BUNDLE_OK) s = run_step(c, kModeAdvect, R, 1 - R);
+            if (s != BUNDLE_OK) return s;
+            CUDA_TRY(&c->err, launch_advance_iter(c->d_iter, c->stream));
             c->cur_P = 1 - R;
             c->cur_R = R;
+        } else if (c->use_graphs && !c->prof) {
+            if (!c->gexec[R] && (s = build_graph(c, R)) != BUNDLE_OK) return s;
+            CUDA_TRY(&c->err, cudaGraphLaunch(c->gexec[R], c->stream));
+            R = 1 - R;
         } else {
+            if ((s = launch_iteration(c, R)) != BUNDLE_OK) return s;
             R = 1 - R;
         }
+        c->iteration += 1;
     }
     c->have_density = true;
     return BUNDLE_OK;
@@ -800,7 +902,7 @@ bundle_status bundle_fetch(bundle_ctx* c, int64_t* off, float* xy, int64_t cap,
             target = c->fetch_xy;
         }
         const double inv = 1.0 / c->map[2];
-        CUDA_TRY(&c->err, launch_layout_to_caller(c->perm, c->cnt[sel], c->pts[sel], c->E, c->cap,
+        CUDA_TRY(&c->err, launch_layout_to_caller(c->perm, c->cnt[sel], c->pts[sel], c->E, c->eb, c->cap,
                                                   c->fetch_off, target, pix ? 0 : 1,
                                                   (float)c->map[3], (float)c->map[4], (float)inv,
                                                   (float)c->map[0], (float)c->map[1], c->stream));

@@ -9,9 +9,9 @@
 
 namespace heb {
 
-// Point layout. Edges live in blocks of kEdgesPerBlock consecutive (spatially
-// sorted) slots; block b owns the point region [b * kEdgesPerBlock * cap,
-// (b+1) * kEdgesPerBlock * cap) of a float2 buffer, and packs its edges'
+// Point layout. Edges live in blocks of `eb` consecutive (spatially sorted)
+// slots, eb <= kEdgesPerBlock chosen per context; block b owns the point region
+// [b * eb * cap, (b+1) * eb * cap) of a float2 buffer, and packs its edges'
 // polylines back to back inside it, in slot order. Only the per-slot point
 // counts are stored: a block recovers its edges' offsets with one scan.
 constexpr int kEdgesPerBlock = 128;
@@ -42,9 +42,12 @@ struct StepArgs {
     uint32_t* hist;          // [G][H][W] histogram accumulated by the splat
     unsigned long long* n_splat;  // running count of splatted points
     int64_t E;
+    int32_t eb;              // edges per block (<= kEdgesPerBlock)
     int32_t cap;             // points per slot of the region (n_fixed or n_max)
     int32_t W, H, G;
-    float h;                 // step magnitude h_i
+    float h;                 // step magnitude h_i (used when h_sched is null)
+    const float* h_sched;    // device schedule h_0, h_1, ... (graph-captured launches)
+    const int32_t* iter;     // device index of the current iteration into h_sched
     float eps;               // Eq. 5 epsilon
     int32_t tries;           // step sizes tried
     float lap_keep;          // 1 - beta
@@ -99,20 +102,24 @@ cudaError_t launch_gather_edges(const int32_t* perm, int64_t E, const int32_t* g
                                 const int32_t* weight_in, int32_t* group_out,
                                 int32_t* weight_out, cudaStream_t st);
 cudaError_t launch_straight_layout(const int32_t* perm, int64_t E, const float2* src,
-                                   const float2* dst, int32_t cap, int32_t* cnt, float2* pts,
-                                   cudaStream_t st);
+                                   const float2* dst, int32_t eb, int32_t cap, int32_t* cnt,
+                                   float2* pts, cudaStream_t st);
 cudaError_t launch_polyline_layout(const int32_t* perm, int64_t E, const int64_t* off,
-                                   const float2* xy, int32_t cap, int32_t* cnt, float2* pts,
-                                   cudaStream_t st);
+                                   const float2* xy, int32_t eb, int32_t cap, int32_t* cnt,
+                                   float2* pts, cudaStream_t st);
 cudaError_t launch_counts_to_caller(const int32_t* perm, const int32_t* cnt, int64_t E,
                                     int64_t* off_out, cudaStream_t st);
 cudaError_t launch_scan_offsets(int64_t* off, int64_t E, int64_t* tmp, cudaStream_t st);
 cudaError_t launch_layout_to_caller(const int32_t* perm, const int32_t* cnt, const float2* pts,
-                                    int64_t E, int32_t cap, const int64_t* off, float2* xy_out,
+                                    int64_t E, int32_t eb, int32_t cap, const int64_t* off,
+                                    float2* xy_out,
                                     int32_t to_world, float ox, float oy, float inv_scale,
                                     float xmin, float ymin, cudaStream_t st);
 cudaError_t launch_sum_counts(const int32_t* cnt, int64_t E, unsigned long long* total,
                               cudaStream_t st);
+// Device iteration counter used with the device schedule of h (graph-friendly).
+cudaError_t launch_set_iter(int32_t* iter, int32_t value, cudaStream_t st);
+cudaError_t launch_advance_iter(int32_t* iter, cudaStream_t st);
 size_t scan_offsets_tmp_elems(int64_t E);
 
 // Message returned by bundle_last_error(NULL) on this thread.

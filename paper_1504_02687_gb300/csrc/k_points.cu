@@ -180,7 +180,7 @@ __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at
 }
 constexpr int kRounds = kMaxCap / 32;  // lanes cover a polyline in this many rounds
 
-// One block of kEdgesPerBlock slots per CTA, staged through shared memory in
+// One block of eb slots per CTA, staged through shared memory in
 // batches of whole polylines:
 //  1. load the batch's points (coalesced), map each point to its polyline;
 //  2. advection, one thread per point, in place (a point reads only itself);
@@ -203,11 +203,12 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     __shared__ unsigned char s_pe[kBatchPoints];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t e0 = (int64_t)blockIdx.x * kEdgesPerBlock;
-    const int nb = (int)min((int64_t)kEdgesPerBlock, a.E - e0);
-    const int64_t region = (int64_t)blockIdx.x * kEdgesPerBlock * a.cap;
+    const int64_t e0 = (int64_t)blockIdx.x * a.eb;
+    const int nb = (int)min((int64_t)a.eb, a.E - e0);
+    const int64_t region = (int64_t)blockIdx.x * a.eb * a.cap;
     const int64_t QC = quad_elems(a.W, a.H);
     const size_t hist_copy = blockIdx.x % kHistCopies;
+    const float h = a.h_sched ? __ldg(a.h_sched + __ldg(a.iter)) : a.h;
 
     for (int i = tid; i < nb; i += kStepThreads) {
         s_cnt[i] = a.cnt_in[e0 + i];
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                 const int j = p0 + k - s_loc[i];
                 if (j > 0 && j < s_cnt[i] - 1) {
                     const T* Q = static_cast<const T*>(a.quads) + (int64_t)s_grp[i] * QC * 4;
-                    s_pts[k] = advect_point(s_pts[k], Q, a.W, a.H, a.h, a.eps, a.tries);
+                    s_pts[k] = advect_point(s_pts[k], Q, a.W, a.H, h, a.eps, a.tries);
                 }
             }
             __syncthreads();
@@ -353,7 +354,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
 template <typename T>
 cudaError_t launch_step_t(int mode, const StepArgs& a, cudaStream_t st) {
     if (a.E <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((a.E + kEdgesPerBlock - 1) / kEdgesPerBlock));
+    if (a.eb < 1 || a.eb > kEdgesPerBlock) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((a.E + a.eb - 1) / a.eb));
     switch (mode) {
         case kModeResample: k_step<kModeResample, T><<<grid, kStepThreads, 0, st>>>(a); break;
         case kModeAdvect: k_step<kModeAdvect, T><<<grid, kStepThreads, 0, st>>>(a); break;
@@ -434,12 +436,12 @@ __global__ void k_gather_edges(const int32_t* __restrict__ perm, int64_t E,
 // Straight edges (2 points each) into the block layout.
 __global__ void k_straight_layout(const int32_t* __restrict__ perm, int64_t E,
                                   const float2* __restrict__ src, const float2* __restrict__ dst,
-                                  int32_t cap, int32_t* cnt, float2* pts) {
+                                  int32_t eb, int32_t cap, int32_t* cnt, float2* pts) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= E) return;
     int32_t e = perm[s];
-    int64_t b = s / kEdgesPerBlock, i = s % kEdgesPerBlock;
-    float2* q = pts + b * kEdgesPerBlock * (int64_t)cap + 2 * i;
+    int64_t b = s / eb, i = s % eb;
+    float2* q = pts + b * eb * (int64_t)cap + 2 * i;
     q[0] = src[e];
     q[1] = dst[e];
     cnt[s] = 2;
@@ -448,12 +450,12 @@ __global__ void k_straight_layout(const int32_t* __restrict__ perm, int64_t E,
 // Caller CSR polylines into the block layout: one block of slots per CTA.
 __global__ void k_polyline_layout(const int32_t* __restrict__ perm, int64_t E,
                                   const int64_t* __restrict__ off, const float2* __restrict__ xy,
-                                  int32_t cap, int32_t* cnt, float2* pts) {
+                                  int32_t eb, int32_t cap, int32_t* cnt, float2* pts) {
     __shared__ int s_n[kEdgesPerBlock];
     __shared__ int s_o[kEdgesPerBlock + 1];
     __shared__ int s_wtot[32];
-    const int64_t s0 = (int64_t)blockIdx.x * kEdgesPerBlock;
-    const int nb = (int)min((int64_t)kEdgesPerBlock, E - s0);
+    const int64_t s0 = (int64_t)blockIdx.x * eb;
+    const int nb = (int)min((int64_t)eb, E - s0);
     const int tid = threadIdx.x;
     if (tid < nb) {
         int32_t e = perm[s0 + tid];
@@ -463,7 +465,7 @@ __global__ void k_polyline_layout(const int32_t* __restrict__ perm, int64_t E,
     block_scan_excl(s_n, s_o, nb, s_wtot);
     if (tid < nb) {
         int32_t e = perm[s0 + tid];
-        float2* q = pts + (int64_t)blockIdx.x * kEdgesPerBlock * cap + s_o[tid];
+        float2* q = pts + (int64_t)blockIdx.x * eb * cap + s_o[tid];
         for (int j = 0; j < s_n[tid]; ++j) q[j] = xy[off[e] + j];
         cnt[s0 + tid] = s_n[tid];
     }
@@ -539,21 +541,22 @@ __global__ void k_scan_apply(int64_t* v, int64_t n, const int64_t* sums) {
 
 __global__ void k_layout_to_caller(const int32_t* __restrict__ perm,
                                    const int32_t* __restrict__ cnt,
-                                   const float2* __restrict__ pts, int64_t E, int32_t cap,
+                                   const float2* __restrict__ pts, int64_t E, int32_t eb,
+                                   int32_t cap,
                                    const int64_t* __restrict__ off, float2* xy, int32_t to_world,
                                    float ox, float oy, float inv_scale, float xmin, float ymin) {
     __shared__ int s_n[kEdgesPerBlock];
     __shared__ int s_o[kEdgesPerBlock + 1];
     __shared__ int s_wtot[32];
-    const int64_t s0 = (int64_t)blockIdx.x * kEdgesPerBlock;
-    const int nb = (int)min((int64_t)kEdgesPerBlock, E - s0);
+    const int64_t s0 = (int64_t)blockIdx.x * eb;
+    const int nb = (int)min((int64_t)eb, E - s0);
     const int tid = threadIdx.x;
     if (tid < nb) s_n[tid] = cnt[s0 + tid];
     __syncthreads();
     block_scan_excl(s_n, s_o, nb, s_wtot);
     if (tid < nb) {
         int32_t e = perm[s0 + tid];
-        const float2* q = pts + (int64_t)blockIdx.x * kEdgesPerBlock * cap + s_o[tid];
+        const float2* q = pts + (int64_t)blockIdx.x * eb * cap + s_o[tid];
         float2* d = xy + off[e];
         for (int j = 0; j < s_n[tid]; ++j) {
             float2 p = q[j];
@@ -576,6 +579,9 @@ __global__ void k_sum_counts(const int32_t* __restrict__ cnt, int64_t E,
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
 }
+
+__global__ void k_set_iter(int32_t* iter, int32_t value) { *iter = value; }
+__global__ void k_advance_iter(int32_t* iter) { *iter += 1; }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -617,17 +623,17 @@ cudaError_t launch_gather_edges(const int32_t* perm, int64_t E, const int32_t* g
 }
 
 cudaError_t launch_straight_layout(const int32_t* perm, int64_t E, const float2* src,
-                                   const float2* dst, int32_t cap, int32_t* cnt, float2* pts,
-                                   cudaStream_t st) {
-    k_straight_layout<<<blocks_for(E, 256), 256, 0, st>>>(perm, E, src, dst, cap, cnt, pts);
+                                   const float2* dst, int32_t eb, int32_t cap, int32_t* cnt,
+                                   float2* pts, cudaStream_t st) {
+    k_straight_layout<<<blocks_for(E, 256), 256, 0, st>>>(perm, E, src, dst, eb, cap, cnt, pts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_polyline_layout(const int32_t* perm, int64_t E, const int64_t* off,
-                                   const float2* xy, int32_t cap, int32_t* cnt, float2* pts,
-                                   cudaStream_t st) {
-    k_polyline_layout<<<blocks_for(E, kEdgesPerBlock), kEdgesPerBlock, 0, st>>>(perm, E, off, xy,
-                                                                               cap, cnt, pts);
+                                   const float2* xy, int32_t eb, int32_t cap, int32_t* cnt,
+                                   float2* pts, cudaStream_t st) {
+    k_polyline_layout<<<blocks_for(E, eb), kEdgesPerBlock, 0, st>>>(perm, E, off, xy, eb, cap,
+                                                                  cnt, pts);
     return cudaGetLastError();
 }
 
@@ -649,11 +655,21 @@ cudaError_t launch_scan_offsets(int64_t* off, int64_t E, int64_t* tmp, cudaStrea
 }
 
 cudaError_t launch_layout_to_caller(const int32_t* perm, const int32_t* cnt, const float2* pts,
-                                    int64_t E, int32_t cap, const int64_t* off, float2* xy_out,
-                                    int32_t to_world, float ox, float oy, float inv_scale,
-                                    float xmin, float ymin, cudaStream_t st) {
-    k_layout_to_caller<<<blocks_for(E, kEdgesPerBlock), kEdgesPerBlock, 0, st>>>(
-        perm, cnt, pts, E, cap, off, xy_out, to_world, ox, oy, inv_scale, xmin, ymin);
+                                    int64_t E, int32_t eb, int32_t cap, const int64_t* off,
+                                    float2* xy_out, int32_t to_world, float ox, float oy,
+                                    float inv_scale, float xmin, float ymin, cudaStream_t st) {
+    k_layout_to_caller<<<blocks_for(E, eb), kEdgesPerBlock, 0, st>>>(
+        perm, cnt, pts, E, eb, cap, off, xy_out, to_world, ox, oy, inv_scale, xmin, ymin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_iter(int32_t* iter, int32_t value, cudaStream_t st) {
+    k_set_iter<<<1, 1, 0, st>>>(iter, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_iter(int32_t* iter, cudaStream_t st) {
+    k_advance_iter<<<1, 1, 0, st>>>(iter);
     return cudaGetLastError();
 }
 

@@ -279,6 +279,27 @@ def test_device_inputs_and_outputs():
         pkg.bundle_destroy(ctx_d)
 
 
+def test_graph_path_equals_separate_launches():
+    """Steady-state iterations run as CUDA graphs unless per-kernel profiling is on; both
+    paths give the same bits."""
+    w = synth.tiny(**WORKLOADS["g5-bylength-r2k4"])
+    p = params_for(w)
+    a = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    b = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    try:
+        pkg.bundle_profile_enable(b, True)
+        pkg.bundle_iterate(a, 6)
+        pkg.bundle_iterate(b, 6)
+        np.testing.assert_array_equal(pkg.bundle_fetch(a, pixels=True)[1],
+                                      pkg.bundle_fetch(b, pixels=True)[1])
+        np.testing.assert_array_equal(pkg.bundle_fetch_density(a, pkg.DENSITY_RHO),
+                                      pkg.bundle_fetch_density(b, pkg.DENSITY_RHO))
+        assert pkg.bundle_get_info(a).iteration == 6
+    finally:
+        pkg.bundle_destroy(a)
+        pkg.bundle_destroy(b)
+
+
 def test_profile_counts_launches():
     w, p, ctx = _make("g1-fixed32")
     try:
