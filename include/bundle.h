@@ -167,7 +167,41 @@ bundle_status bundle_fetch(bundle_ctx* ctx, int64_t* off, float* xy, int64_t cap
 bundle_status bundle_fetch_density(bundle_ctx* ctx, int32_t which, void* dst, int64_t dst_bytes,
                                    int32_t flags);
 
-/* Sizes, widths, map, schedule and point counts of a context (synchronises the stream). */
+/*
+ * Batched form: many independent graphs bundled together. Each graph has its
+ * own edges, groups, grid and parameters (the paper bundles one graph at a
+ * time; batching serves many small graphs at once). The batch context owns one
+ * member context per graph (own buffers and stream); bundle_iterate on the
+ * batch runs every member, and each steady-state iteration of all members is
+ * one CUDA graph launch with one branch per member, so small graphs run side
+ * by side on the GPU. Fetch results through bundle_batch_member.
+ */
+typedef struct {
+    int64_t n_edges;
+    const float* src_xy;   /* float [2 * n_edges], world coordinates */
+    const float* dst_xy;
+    const int32_t* group;  /* nullable */
+    int32_t n_groups;
+    const int32_t* weight; /* nullable */
+} bundle_graph_desc;
+
+/* Create a batch of n_graphs (1..4096) graphs; params holds one bundle_params per
+ * graph. flags as bundle_init (applies to every graph). On failure *out is NULL and
+ * bundle_last_error(NULL) names the graph. */
+bundle_status bundle_init_batch(bundle_ctx** out, int32_t n_graphs,
+                                const bundle_graph_desc* graphs, const bundle_params* params,
+                                int32_t flags, void* stream);
+
+/* Number of graphs of a batch (0 for a single-graph context). */
+int32_t bundle_batch_size(const bundle_ctx* ctx);
+
+/* Borrowed handle of graph k of a batch (NULL if out of range), valid until the
+ * batch is destroyed: bundle_fetch, bundle_fetch_density and bundle_get_info work
+ * on it; bundle_iterate on a member returns ESTATE, bundle_destroy ignores it. */
+bundle_ctx* bundle_batch_member(bundle_ctx* ctx, int32_t k);
+
+/* Sizes, widths, map, schedule and point counts of a context (synchronises the stream).
+ * For a batch: sums of the counts over its graphs; sizes and map of graph 0. */
 bundle_status bundle_get_info(const bundle_ctx* ctx, bundle_info* out);
 
 /*

@@ -32,7 +32,8 @@ PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "c
 EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bundle_iterate",
             "bundle_fetch", "bundle_fetch_density", "bundle_get_info", "bundle_sync",
             "bundle_destroy", "bundle_last_error", "bundle_status_string",
-            "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc")
+            "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc",
+            "bundle_init_batch", "bundle_batch_size", "bundle_batch_member")
 
 
 class BundleParams(ctypes.Structure):
@@ -59,6 +60,14 @@ class BundleInfo(ctypes.Structure):
         ("sum_bits", ctypes.c_int32), ("rho_dtype", ctypes.c_int32),
         ("iteration", ctypes.c_int32), ("map", ctypes.c_double * 5), ("h_next", ctypes.c_double),
         ("device_bytes", ctypes.c_int64), ("points_processed", ctypes.c_int64),
+    ]
+
+
+class BundleGraphDesc(ctypes.Structure):
+    """Mirror of ``bundle_graph_desc``."""
+    _fields_ = [
+        ("n_edges", ctypes.c_int64), ("src_xy", ctypes.c_void_p), ("dst_xy", ctypes.c_void_p),
+        ("group", ctypes.c_void_p), ("n_groups", ctypes.c_int32), ("weight", ctypes.c_void_p),
     ]
 
 
@@ -111,6 +120,13 @@ def lib():
     L.bundle_profile_read.restype = i32
     L.bundle_smooth_noalloc.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P]
     L.bundle_smooth_noalloc.restype = i32
+    L.bundle_init_batch.argtypes = [ctypes.POINTER(P), i32, ctypes.POINTER(BundleGraphDesc), pp,
+                                    i32, P]
+    L.bundle_init_batch.restype = i32
+    L.bundle_batch_size.argtypes = [P]
+    L.bundle_batch_size.restype = i32
+    L.bundle_batch_member.argtypes = [P, i32]
+    L.bundle_batch_member.restype = P
     _lib = L
     return L
 
@@ -200,6 +216,40 @@ def bundle_init_polylines(params: BundleParams, off, xy_px, group=None, n_groups
                                      _stream_handle(stream))
     _check(st)
     return ctx
+
+
+def bundle_init_batch(graphs, params, stream=None):
+    """Create a batch. graphs: list of dicts with src_xy, dst_xy, group, n_groups, weight
+    (numpy, host); params: list of BundleParams (one per graph). Returns the batch handle."""
+    keep = []
+    descs = (BundleGraphDesc * len(graphs))()
+    for d, g in zip(descs, graphs):
+        arrs = [_host(g["src_xy"], np.float32), _host(g["dst_xy"], np.float32),
+                _host(g.get("group"), np.int32), _host(g.get("weight"), np.int32)]
+        keep.append(arrs)
+        d.n_edges = int(arrs[0].shape[0])
+        d.src_xy, d.dst_xy = arrs[0].ctypes.data, arrs[1].ctypes.data
+        d.group = None if arrs[2] is None else arrs[2].ctypes.data
+        d.weight = None if arrs[3] is None else arrs[3].ctypes.data
+        d.n_groups = int(g.get("n_groups", 1))
+    parr = (BundleParams * len(params))(*params)
+    ctx = ctypes.c_void_p()
+    st = lib().bundle_init_batch(ctypes.byref(ctx), len(graphs), descs, parr, 0,
+                                 _stream_handle(stream))
+    _check(st)
+    return ctx
+
+
+def bundle_batch_size(ctx) -> int:
+    return int(lib().bundle_batch_size(ctx))
+
+
+def bundle_batch_member(ctx, k: int):
+    """Borrowed handle of graph k of a batch (valid until the batch is destroyed)."""
+    h = lib().bundle_batch_member(ctx, int(k))
+    if not h:
+        raise IndexError(k)
+    return ctypes.c_void_p(h)
 
 
 def bundle_iterate(ctx, n_iters: int):

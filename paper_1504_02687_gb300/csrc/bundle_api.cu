@@ -60,6 +60,13 @@ struct bundle_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool use_graphs = true;
+    // batch of independent graphs (bundle_init_batch): each member is a full context with
+    // its own buffers and stream; a steady-state iteration of all members is one CUDA graph
+    // with one branch per member
+    std::vector<bundle_ctx*> members;
+    bool is_member = false;
+    cudaGraphExec_t bexec[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> bev;  // fork/join events
     // per-kernel event timing (bundle_profile_enable)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -118,6 +125,11 @@ cudaError_t dalloc(bundle_ctx* c, T** ptr, size_t n) {
 
 void free_ctx(bundle_ctx* c) {
     if (!c) return;
+    for (bundle_ctx* m : c->members) {
+        m->is_member = false;
+        free_ctx(m);
+    }
+    c->members.clear();
     if (c->device < 0) {
         delete c;
         return;
@@ -132,6 +144,9 @@ void free_ctx(bundle_ctx* c) {
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     for (cudaGraphExec_t g : c->gexec)
         if (g) cudaGraphExecDestroy(g);
+    for (cudaGraphExec_t g : c->bexec)
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t ev : c->bev) cudaEventDestroy(ev);
     if (c->h_sched) cudaFree(c->h_sched);
     if (c->d_iter) cudaFree(c->d_iter);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -810,11 +825,7 @@ bundle_status bundle_init_polylines(bundle_ctx** out, const bundle_params* p, in
     return BUNDLE_OK;
 }
 
-bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
-    if (!c) return BUNDLE_EINVAL;
-    if (n_iters < 0) return fail(&c->err, BUNDLE_EINVAL, "n_iters must be >= 0");
-    if (n_iters == 0) return BUNDLE_OK;
-    DeviceGuard dg(c->device);
+static bundle_status iterate_single(bundle_ctx* c, int32_t n_iters) {
     bundle_status s = ensure_schedule(c, c->iteration + n_iters);
     if (s != BUNDLE_OK) return s;
     CUDA_TRY(&c->err, launch_set_iter(c->d_iter, c->iteration, c->stream));
@@ -846,9 +857,184 @@ bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
     return BUNDLE_OK;
 }
 
+
+// Fork: every member stream waits for the work queued so far on `from`.
+static bundle_status batch_fork(bundle_ctx* c, cudaStream_t from) {
+    CUDA_TRY(&c->err, cudaEventRecord(c->bev[0], from));
+    for (bundle_ctx* m : c->members) CUDA_TRY(&c->err, cudaStreamWaitEvent(m->stream, c->bev[0], 0));
+    return BUNDLE_OK;
+}
+
+// Join: `into` waits for every member stream.
+static bundle_status batch_join(bundle_ctx* c, cudaStream_t into) {
+    for (size_t k = 0; k < c->members.size(); ++k) {
+        CUDA_TRY(&c->err, cudaEventRecord(c->bev[k + 1], c->members[k]->stream));
+        CUDA_TRY(&c->err, cudaStreamWaitEvent(into, c->bev[k + 1], 0));
+    }
+    return BUNDLE_OK;
+}
+
+// One steady-state iteration of every member, each on its own branch, as one graph.
+static bundle_status build_batch_graph(bundle_ctx* c, int R) {
+    if (!c->cap_stream)
+        CUDA_TRY(&c->err, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> saved;
+    for (bundle_ctx* m : c->members) {
+        if (!m->cap_stream)
+            CUDA_TRY(&c->err, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(&c->err, BUNDLE_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+    bundle_status s = BUNDLE_OK;
+    for (bundle_ctx* m : c->members) saved.push_back(m->stream);
+    for (bundle_ctx* m : c->members) m->stream = m->cap_stream;
+    if (s == BUNDLE_OK) s = batch_fork(c, c->cap_stream);
+    for (size_t k = 0; k < c->members.size() && s == BUNDLE_OK; ++k) {
+        s = launch_iteration(c->members[k], R);
+        if (s != BUNDLE_OK) c->err = "member " + std::to_string(k) + ": " + c->members[k]->err;
+    }
+    if (s == BUNDLE_OK) s = batch_join(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    for (size_t k = 0; k < c->members.size(); ++k) c->members[k]->stream = saved[k];
+    if (s != BUNDLE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e2 != cudaSuccess)
+        return fail(&c->err, BUNDLE_ECUDA, "batch capture end: %s", cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&c->bexec[R], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->bexec[R] = nullptr;
+        return fail(&c->err, BUNDLE_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return BUNDLE_OK;
+}
+
+static bundle_status iterate_batch(bundle_ctx* c, int32_t n_iters) {
+    bundle_status s = batch_fork(c, c->stream);
+    if (s != BUNDLE_OK) return s;
+    const bool graphs = c->use_graphs && !c->prof && n_iters > 1;
+    if (!graphs) {
+        // every member runs its own iterations on its stream, concurrently
+        for (size_t k = 0; k < c->members.size(); ++k)
+            if ((s = iterate_single(c->members[k], n_iters)) != BUNDLE_OK) {
+                c->err = "member " + std::to_string(k) + ": " + c->members[k]->err;
+                return s;
+            }
+        return batch_join(c, c->stream);
+    }
+    // members in lockstep: resample + splat on each stream, then n - 1 batch graphs, then
+    // the last iteration's filter and advection on each stream
+    int R = -1;
+    for (size_t k = 0; k < c->members.size(); ++k) {
+        bundle_ctx* m = c->members[k];
+        const float* before = m->h_sched;
+        if ((s = ensure_schedule(m, m->iteration + n_iters)) != BUNDLE_OK) return s;
+        if (m->h_sched != before)  // the batch graphs captured the old schedule
+            for (cudaGraphExec_t& g : c->bexec)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
+        CUDA_TRY(&m->err, launch_set_iter(m->d_iter, m->iteration, m->stream));
+        if ((s = run_step(m, kModeResample, m->cur_P, 1 - m->cur_P)) != BUNDLE_OK) return s;
+        if (R < 0) R = 1 - m->cur_P;
+        if (1 - m->cur_P != R) return fail(&c->err, BUNDLE_ESTATE, "batch members out of step");
+    }
+    if ((s = batch_join(c, c->stream)) != BUNDLE_OK) return s;
+    for (int32_t it = 0; it + 1 < n_iters; ++it) {
+        if (!c->bexec[R] && (s = build_batch_graph(c, R)) != BUNDLE_OK) return s;
+        CUDA_TRY(&c->err, cudaGraphLaunch(c->bexec[R], c->stream));
+        R = 1 - R;
+    }
+    if ((s = batch_fork(c, c->stream)) != BUNDLE_OK) return s;
+    for (bundle_ctx* m : c->members) {
+        if ((s = run_filter(m)) == BUNDLE_OK) s = run_step(m, kModeAdvect, R, 1 - R);
+        if (s != BUNDLE_OK) return s;
+        CUDA_TRY(&m->err, launch_advance_iter(m->d_iter, m->stream));
+        m->cur_P = 1 - R;
+        m->cur_R = R;
+        m->iteration += n_iters;
+        m->have_density = true;
+    }
+    return batch_join(c, c->stream);
+}
+
+bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
+    if (!c) return BUNDLE_EINVAL;
+    if (c->is_member)
+        return fail(&c->err, BUNDLE_ESTATE, "a batch member iterates with its batch");
+    if (n_iters < 0) return fail(&c->err, BUNDLE_EINVAL, "n_iters must be >= 0");
+    if (n_iters == 0) return BUNDLE_OK;
+    DeviceGuard dg(c->device);
+    if (!c->members.empty()) {
+        bundle_status s = iterate_batch(c, n_iters);
+        if (s == BUNDLE_OK) {
+            c->iteration += n_iters;
+            c->have_density = true;
+        }
+        return s;
+    }
+    return iterate_single(c, n_iters);
+}
+
+bundle_status bundle_init_batch(bundle_ctx** out, int32_t n_graphs, const bundle_graph_desc* graphs,
+                                const bundle_params* params, int32_t flags, void* stream) {
+    std::string* e = &g_init_error;
+    if (!out) return fail(e, BUNDLE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_graphs < 1 || n_graphs > 4096 || !graphs || !params)
+        return fail(e, BUNDLE_EINVAL, "need 1..4096 graphs with their parameters");
+    bundle_ctx* c = new (std::nothrow) bundle_ctx();
+    if (!c) return fail(e, BUNDLE_ENOMEM, "host allocation failed");
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->device = -1;
+    bundle_status s = attach_cuda(c, e);
+    if (s != BUNDLE_OK) {
+        free_ctx(c);
+        return s;
+    }
+    for (int32_t k = 0; k < n_graphs; ++k) {
+        bundle_ctx* m = nullptr;
+        const bundle_graph_desc& g = graphs[k];
+        s = bundle_init(&m, &params[k], g.n_edges, g.src_xy, g.dst_xy, g.group, g.n_groups,
+                        g.weight, flags, nullptr);
+        if (s != BUNDLE_OK) {
+            std::string msg = "graph " + std::to_string(k) + ": " + *e;
+            free_ctx(c);
+            *e = msg;
+            return s;
+        }
+        m->is_member = true;
+        c->members.push_back(m);
+        c->E += m->E;
+    }
+    c->bev.resize(c->members.size() + 1);
+    for (cudaEvent_t& ev : c->bev)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            free_ctx(c);
+            return fail(e, BUNDLE_ECUDA, "event creation failed");
+        }
+    c->G = c->members[0]->G;
+    c->W = c->members[0]->W;
+    c->H = c->members[0]->H;
+    *out = c;
+    return BUNDLE_OK;
+}
+
+int32_t bundle_batch_size(const bundle_ctx* c) { return c ? (int32_t)c->members.size() : 0; }
+
+bundle_ctx* bundle_batch_member(bundle_ctx* c, int32_t k) {
+    if (!c || k < 0 || k >= (int32_t)c->members.size()) return nullptr;
+    return c->members[(size_t)k];
+}
+
 bundle_status bundle_sync(bundle_ctx* c) {
     if (!c) return BUNDLE_EINVAL;
     DeviceGuard dg(c->device);
+    for (bundle_ctx* m : c->members) CUDA_TRY(&c->err, cudaStreamSynchronize(m->stream));
     CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
     CUDA_TRY(&c->err, cudaGetLastError());
     return BUNDLE_OK;
@@ -857,6 +1043,8 @@ bundle_status bundle_sync(bundle_ctx* c) {
 bundle_status bundle_fetch(bundle_ctx* c, int64_t* off, float* xy, int64_t cap,
                            int64_t* n_points, int32_t flags) {
     if (!c) return BUNDLE_EINVAL;
+    if (!c->members.empty())
+        return fail(&c->err, BUNDLE_ESTATE, "fetch a batch's graphs through bundle_batch_member");
     if (!off || !n_points) return fail(&c->err, BUNDLE_EINVAL, "off and n_points are required");
     int sel = c->cur_P;
     if (flags & BUNDLE_FETCH_RESAMPLED) {
@@ -917,6 +1105,8 @@ bundle_status bundle_fetch(bundle_ctx* c, int64_t* off, float* xy, int64_t cap,
 bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int64_t dst_bytes,
                                    int32_t flags) {
     if (!c) return BUNDLE_EINVAL;
+    if (!c->members.empty())
+        return fail(&c->err, BUNDLE_ESTATE, "fetch a batch's graphs through bundle_batch_member");
     if (!dst) return fail(&c->err, BUNDLE_EINVAL, "dst is NULL");
     if (!c->have_density) return fail(&c->err, BUNDLE_ESTATE, "no iteration has run");
     const size_t C = (size_t)c->G * c->H * c->W;
@@ -944,6 +1134,22 @@ bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int6
 
 bundle_status bundle_get_info(const bundle_ctx* c, bundle_info* out) {
     if (!c || !out) return BUNDLE_EINVAL;
+    if (!c->members.empty()) {
+        // a batch reports the sums over its graphs; sizes and map are those of graph 0
+        bundle_status s = bundle_get_info(c->members[0], out);
+        if (s != BUNDLE_OK) return s;
+        for (size_t k = 1; k < c->members.size(); ++k) {
+            bundle_info mi;
+            if ((s = bundle_get_info(c->members[k], &mi)) != BUNDLE_OK) return s;
+            out->n_edges += mi.n_edges;
+            out->n_points += mi.n_points;
+            out->n_points_resampled += mi.n_points_resampled;
+            out->device_bytes += mi.device_bytes;
+            out->points_processed += mi.points_processed;
+        }
+        out->iteration = c->iteration;
+        return BUNDLE_OK;
+    }
     bundle_ctx* m = const_cast<bundle_ctx*>(c);
     DeviceGuard dg(c->device);
     std::memset(out, 0, sizeof *out);
@@ -1012,7 +1218,10 @@ bundle_status bundle_profile_read(bundle_ctx* c, double* ms, int64_t* launches, 
     return BUNDLE_OK;
 }
 
-void bundle_destroy(bundle_ctx* c) { free_ctx(c); }
+void bundle_destroy(bundle_ctx* c) {
+    if (c && c->is_member) return;  // members belong to their batch
+    free_ctx(c);
+}
 
 const char* bundle_last_error(const bundle_ctx* c) {
     return c ? c->err.c_str() : g_init_error.c_str();

@@ -64,7 +64,9 @@ def test_struct_mirrors_match_the_c_layout(tmp_path):
     import paper_1504_02687_gb300 as pkg
 
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
-    for cname, cls in (("bundle_params", pkg.BundleParams), ("bundle_info", pkg.BundleInfo)):
+    pairs = (("bundle_params", pkg.BundleParams), ("bundle_info", pkg.BundleInfo),
+             ("bundle_graph_desc", pkg.BundleGraphDesc))
+    for cname, cls in pairs:
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
             cf = "lambda" if f == "lambda_" else f
@@ -76,7 +78,7 @@ def test_struct_mirrors_match_the_c_layout(tmp_path):
     subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
     got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                  check=True).stdout.splitlines())
-    for cname, cls in (("bundle_params", pkg.BundleParams), ("bundle_info", pkg.BundleInfo)):
+    for cname, cls in pairs:
         assert int(got[cname]) == ctypes.sizeof(cls)
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)

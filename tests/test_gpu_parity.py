@@ -300,6 +300,45 @@ def test_graph_path_equals_separate_launches():
         pkg.bundle_destroy(b)
 
 
+def test_batch_members_equal_single_runs():
+    """A batch of graphs with different grids, groups and parameters gives, for each graph,
+    the same bits as that graph bundled alone -- through the batch graph (one CUDA graph per
+    iteration for all members) and through separate launches (profiling on)."""
+    names = ["g1-fixed32", "g3-bylength-weighted", "g5-bylength-r2k4"]
+    ws = [synth.tiny(**WORKLOADS[n]) for n in names]
+    ps = [params_for(w) for w in ws]
+    descs = [dict(src_xy=w.src_xy, dst_xy=w.dst_xy, group=w.group, n_groups=w.n_groups,
+                  weight=w.weight) for w in ws]
+    for profiled in (False, True):
+        batch = pkg.bundle_init_batch(descs, ps)
+        singles = [pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+                   for w, p in zip(ws, ps)]
+        try:
+            assert pkg.bundle_batch_size(batch) == 3
+            if profiled:
+                pkg.bundle_profile_enable(batch, True)
+            pkg.bundle_iterate(batch, 3)
+            pkg.bundle_iterate(batch, 2)
+            total = 0
+            for k, c in enumerate(singles):
+                pkg.bundle_iterate(c, 5)
+                m = pkg.bundle_batch_member(batch, k)
+                om, xm = pkg.bundle_fetch(m, pixels=True)
+                oc, xc = pkg.bundle_fetch(c, pixels=True)
+                np.testing.assert_array_equal(om, oc)
+                np.testing.assert_array_equal(xm, xc)
+                np.testing.assert_array_equal(pkg.bundle_fetch_density(m, pkg.DENSITY_SUMS),
+                                              pkg.bundle_fetch_density(c, pkg.DENSITY_SUMS))
+                total += pkg.bundle_get_info(c).points_processed
+            assert pkg.bundle_get_info(batch).points_processed == total
+            with pytest.raises(pkg.BundleError):
+                pkg.bundle_iterate(pkg.bundle_batch_member(batch, 0), 1)
+        finally:
+            pkg.bundle_destroy(batch)
+            for c in singles:
+                pkg.bundle_destroy(c)
+
+
 def test_profile_counts_launches():
     w, p, ctx = _make("g1-fixed32")
     try:
