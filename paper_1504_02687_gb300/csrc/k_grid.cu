@@ -83,6 +83,101 @@ __global__ void k_rowbox(const uint32_t* __restrict__ hist, int copies, TS* __re
     for (int x = lane; x < W; x += 32) Y[base + x] = src[x + (x / c) * pad];
 }
 
+// Row passes for rows whose lane chunk c = ceil(W / 32) is C (8, 16 or 32): lane l
+// owns [l*C, l*C + C) and keeps a pass's outputs in registers until the warp has
+// read the pass's input, so a row needs one shared buffer. A table built once per
+// CTA maps every window index t in [-r-1, W+r] to the shared slot of refl(t); the
+// buffer and the table both skip one slot after every C entries, so the 32 lanes,
+// C apart, hit 32 different banks.
+constexpr int kRowWarps = 8;
+
+template <int C>
+__device__ __forceinline__ int padded(int k) { return k + k / C; }
+
+template <typename TS, int C>
+__global__ void __launch_bounds__(32 * kRowWarps)
+    k_rowbox_reg(const uint32_t* __restrict__ hist, int copies, TS* __restrict__ Y, int G, int H,
+                 int W, int r, int passes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int stride = padded<C>(W) + 1;
+    TS* buf = reinterpret_cast<TS*>(smem_raw) + (size_t)warp * stride;
+    int* tab = reinterpret_cast<int*>(reinterpret_cast<TS*>(smem_raw) + (size_t)kRowWarps * stride);
+    const int ntab = W + 2 * r + 2;  // k = t + r + 1 for t = -r-1 .. W+r
+    for (int k = threadIdx.x; k < ntab; k += blockDim.x)
+        tab[padded<C>(k)] = padded<C>(reflect_index(k - r - 1, W));
+    __syncthreads();
+    const int g = blockIdx.y;
+    const int v = blockIdx.x * kRowWarps + warp;
+    if (v >= H) return;
+    const size_t base = ((size_t)g * H + v) * W;
+    const size_t stride_copy = (size_t)G * H * W;
+    if ((W & 3) == 0) {
+        const uint4* h0 = reinterpret_cast<const uint4*>(hist + base);
+        for (int x4 = lane; x4 < (W >> 2); x4 += 32) {
+            uint4 u = __ldg(h0 + x4);
+            for (int k = 1; k < copies; ++k) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4*>(hist + k * stride_copy + base) + x4);
+                u.x += w.x;
+                u.y += w.y;
+                u.z += w.z;
+                u.w += w.w;
+            }
+            const int x = 4 * x4;
+            buf[padded<C>(x)] = (TS)u.x;
+            buf[padded<C>(x + 1)] = (TS)u.y;
+            buf[padded<C>(x + 2)] = (TS)u.z;
+            buf[padded<C>(x + 3)] = (TS)u.w;
+        }
+    } else {
+        for (int x = lane; x < W; x += 32) {
+            TS u = (TS)hist[base + x];
+            for (int k = 1; k < copies; ++k) u += (TS)hist[k * stride_copy + base + x];
+            buf[padded<C>(x)] = u;
+        }
+    }
+    __syncwarp();
+    const int i0 = lane * C;
+    const int len = max(0, min(C, W - i0));
+    const int own = padded<C>(i0);
+    TS out[C];
+    for (int p = 0; p < passes; ++p) {
+        if (len > 0) {
+            TS s = 0;
+            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t) s += buf[tab[padded<C>(t + r + 1)]];
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                if (q < len) {
+                    const int k = i0 + q + r + 1;  // table position of t = i0 + q
+                    s += buf[tab[padded<C>(k + r)]] - buf[tab[padded<C>(k - r - 1)]];
+                    out[q] = s;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+            if (q < len) buf[own + q] = out[q];
+        __syncwarp();
+    }
+    for (int x = lane; x < W; x += 32) Y[base + x] = buf[padded<C>(x)];
+}
+
+template <typename TS, int C>
+cudaError_t rowbox_reg_t(const FilterArgs& a, cudaStream_t st) {
+    const size_t smem = (size_t)kRowWarps * (a.W + a.W / C + 1) * sizeof(TS) +
+                        (size_t)(a.W + 2 * a.r + 2 + (a.W + 2 * a.r + 2) / C + 1) * 4;
+    auto kern = k_rowbox_reg<TS, C>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)((a.H + kRowWarps - 1) / kRowWarps), (unsigned)a.G);
+    kern<<<grid, 32 * kRowWarps, smem, st>>>(a.hist, a.hist_copies < 1 ? 1 : a.hist_copies,
+                                              static_cast<TS*>(a.Y), a.G, a.H, a.W, a.r,
+                                              a.passes);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- column passes
 // One CTA per strip of STRIP columns of one layer, the whole column height in
 // shared memory. Thread (j, ch) owns column j and the 32-row chunk ch; its 32
@@ -99,6 +194,15 @@ __global__ void __launch_bounds__(kColThreads)
              int passes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TS* buf = reinterpret_cast<TS*>(smem_raw);
+    const int nch = (H + kChunk - 1) / kChunk;
+    // tab[k + k/32], k = t + r + 1: shared offset of row refl(t) (padded, times STRIP) for
+    // t = -r-1 .. H+r; the skipped slot every 32 entries keeps the chunks' lookups apart
+    int* tab = reinterpret_cast<int*>(buf + (size_t)(H + nch) * STRIP);
+    const int ntab = H + 2 * r + 2;
+    for (int k = threadIdx.x; k < ntab; k += blockDim.x) {
+        const int q = reflect_index(k - r - 1, H);
+        tab[k + k / kChunk] = (q + q / kChunk) * STRIP;
+    }
     const int g = blockIdx.y;
     const int x0 = blockIdx.x * STRIP;
     const int j = threadIdx.x % STRIP, ch = threadIdx.x / STRIP;
@@ -111,26 +215,27 @@ __global__ void __launch_bounds__(kColThreads)
     __syncthreads();
     const int i0 = ch * kChunk;
     const int len = max(0, min(kChunk, H - i0));
+    auto tl = [&](int t) { const int k = t + r + 1; return tab[k + k / kChunk]; };
+    const TS* col = buf + j;
     TS out[kChunk];
     for (int p = 0; p < passes; ++p) {
         if (len > 0) {
             TS s = 0;
-            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t)
-                s += buf[prow(reflect_index(t, H)) * STRIP + j];
+            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t) s += col[tl(t)];
 #pragma unroll
             for (int q = 0; q < kChunk; ++q) {
                 if (q < len) {
-                    int i = i0 + q;
-                    s += buf[prow(reflect_index(i + r, H)) * STRIP + j] -
-                         buf[prow(reflect_index(i - r - 1, H)) * STRIP + j];
+                    const int i = i0 + q;
+                    s += col[tl(i + r)] - col[tl(i - r - 1)];
                     out[q] = s;
                 }
             }
         }
         __syncthreads();
+        TS* mine = buf + (size_t)prow(i0) * STRIP + j;
 #pragma unroll
         for (int q = 0; q < kChunk; ++q)
-            if (q < len) buf[prow(i0 + q) * STRIP + j] = out[q];
+            if (q < len) mine[q * STRIP] = out[q];
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < H * STRIP; idx += blockDim.x) {
@@ -214,6 +319,9 @@ template <typename TS>
 cudaError_t rowbox_t(const FilterArgs& a, cudaStream_t st) {
     const int c = (a.W + 31) / 32;
     const int pad = (c % 2 == 0) ? 1 : 2;
+    if (c == 32) return rowbox_reg_t<TS, 32>(a, st);
+    if (c == 16) return rowbox_reg_t<TS, 16>(a, st);
+    if (c == 8) return rowbox_reg_t<TS, 8>(a, st);
     const size_t per_row = (size_t)2 * (a.W + 32 * pad) * sizeof(TS);
     size_t fit = (200u * 1024u) / per_row;
     int rows = (int)(fit < 4 ? fit : 4);
@@ -234,7 +342,8 @@ template <typename TS, int STRIP>
 cudaError_t colbox_strip(const FilterArgs& a, cudaStream_t st) {
     const int nch = (a.H + kChunk - 1) / kChunk;
     if (STRIP * nch > kColThreads) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(a.H + nch) * STRIP * sizeof(TS);
+    const int ntab = a.H + 2 * a.r + 2;
+    const size_t smem = (size_t)(a.H + nch) * STRIP * sizeof(TS) + (size_t)(ntab + ntab / kChunk + 1) * 4;
     auto kern = k_colbox<TS, STRIP>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
