@@ -69,6 +69,17 @@ def _load():
                                 i32, i32, f64, f64, f64, i32, i32, i32, P, P, i64, P, P, P, P, P,
                                 i64])
     lib.oracle_run.restype = i64
+    lib.oracle_advect_laplace_mode.argtypes = [i64, P, P, P, i32, i32, i32, P, f64, f64, i32, f64,
+                                               i32, P, P]
+    lib.oracle_advect_laplace_mode.restype = None
+    lib.oracle_combine_matrix.argtypes = [i32, i32, i32, i32, i32, P, P, P]
+    lib.oracle_combine_matrix.restype = None
+    lib.oracle_directed_offset.argtypes = [i64, P, P, f64, i32, i32]
+    lib.oracle_directed_offset.restype = None
+    lib.oracle_run_mode.argtypes = ([i64, P, P, P, P, i32, i32, i32, i32, i32, i32, i32, f64, f64,
+                                     i32, i32, f64, f64, f64, i32, i32, i32, i32, f64, P, P, P,
+                                     i64, P, P, P, P, P, i64])
+    lib.oracle_run_mode.restype = i64
     _lib = lib
     return lib
 
@@ -96,6 +107,8 @@ class Params:
     beta: float = 0.5
     eps: float = 1e-9
     tries: int = 8
+    fixed_step: bool = False      # KDEEB step (Sec. 3.3)
+    directed_offset: float = 0.0  # pixels along the edge normal after the first sampling (Sec. 3)
 
 
 def grid_map(src_xy, dst_xy, grid_w=0, grid_h=0, dominant=800, margin=4):
@@ -190,8 +203,9 @@ def bandwidth(iteration, radius, passes, h_max_sigmas=2.0, lam=0.9):
     return float(_load().oracle_bandwidth(iteration, radius, passes, h_max_sigmas, lam))
 
 
-def advect_laplace(off, xy, group, rho, h, eps=1e-9, tries=8, beta=0.5):
-    """Returns (new_xy, accepted) with accepted[k] = trial index, -1 none, -2 endpoint."""
+def advect_laplace(off, xy, group, rho, h, eps=1e-9, tries=8, beta=0.5, fixed_step=False):
+    """Returns (new_xy, accepted) with accepted[k] = trial index, -1 none, -2 endpoint.
+    fixed_step: KDEEB's step of exactly h with no density test (Sec. 3.3, Fig. 3)."""
     lib = _load()
     off = _c(off, np.int64)
     xy = _c(xy, np.float64).reshape(-1, 2)
@@ -201,9 +215,29 @@ def advect_laplace(off, xy, group, rho, h, eps=1e-9, tries=8, beta=0.5):
     G, H, W = rho.shape
     out = np.zeros_like(xy)
     acc = np.zeros(xy.shape[0], np.int32)
-    lib.oracle_advect_laplace(E, _p(off), _p(xy), _p(group), G, H, W, _p(rho), h, eps, tries, beta,
-                              _p(out), _p(acc))
+    lib.oracle_advect_laplace_mode(E, _p(off), _p(xy), _p(group), G, H, W, _p(rho), h, eps, tries,
+                                   beta, 1 if fixed_step else 0, _p(out), _p(acc))
     return out, acc
+
+
+def combine_matrix(sums, radius, passes, M):
+    """rho_l = sum_b M[l, b] S_b / s^k for a general G x G interaction matrix (Eq. 3)."""
+    lib = _load()
+    sums = _c(sums, np.int64)
+    G, H, W = sums.shape
+    M = _c(M, np.float64).reshape(G, G)
+    rho = np.zeros((G, H, W), np.float64)
+    lib.oracle_combine_matrix(G, H, W, radius, passes, _p(M), _p(sums), _p(rho))
+    return rho
+
+
+def directed_offset(off, xy, amount, W, H):
+    """Shift interior points by `amount` px along their edge's normal (Sec. 3); returns a copy."""
+    lib = _load()
+    off = _c(off, np.int64)
+    xy = np.array(xy, np.float64).reshape(-1, 2)
+    lib.oracle_directed_offset(off.shape[0] - 1, _p(off), _p(xy), float(amount), W, H)
+    return xy
 
 
 @dataclass
@@ -217,8 +251,10 @@ class RunResult:
     res_xy: np.ndarray | None = None
 
 
-def run(off, xy, group, weight, G, H, W, prm: Params, iter0=0, n_iters=1, keep_last=False):
-    """The whole loop: n_iters iterations from polylines (off, xy) in pixel units."""
+def run(off, xy, group, weight, G, H, W, prm: Params, iter0=0, n_iters=1, keep_last=False,
+        M=None):
+    """The whole loop: n_iters iterations from polylines (off, xy) in pixel units. M: optional
+    G x G interaction matrix replacing Eq. 4's."""
     lib = _load()
     off = _c(off, np.int64)
     xy = _c(xy, np.float64).reshape(-1, 2)
@@ -236,11 +272,13 @@ def run(off, xy, group, weight, G, H, W, prm: Params, iter0=0, n_iters=1, keep_l
         rho = np.zeros((G, H, W), np.float64)
         res_off = np.zeros(E + 1, np.int64)
         res_xy = np.zeros((cap, 2), np.float64)
-    n = lib.oracle_run(E, _p(off), _p(xy), _p(group), _p(weight), G, H, W, prm.radius, prm.passes,
-                       prm.alpha_num, prm.alpha_den, prm.h_max_sigmas, prm.lam, prm.n_fixed,
-                       prm.n_max, prm.delta, prm.beta, prm.eps, prm.tries, iter0, n_iters,
-                       _p(off_o), _p(xy_o), cap, _p(hist), _p(sums), _p(rho), _p(res_off),
-                       _p(res_xy), cap)
+    Mc = None if M is None else _c(M, np.float64).reshape(G, G)
+    n = lib.oracle_run_mode(E, _p(off), _p(xy), _p(group), _p(weight), G, H, W, prm.radius,
+                            prm.passes, prm.alpha_num, prm.alpha_den, prm.h_max_sigmas, prm.lam,
+                            prm.n_fixed, prm.n_max, prm.delta, prm.beta, prm.eps, prm.tries, iter0,
+                            n_iters, 1 if prm.fixed_step else 0, float(prm.directed_offset),
+                            _p(Mc), _p(off_o), _p(xy_o), cap, _p(hist), _p(sums), _p(rho),
+                            _p(res_off), _p(res_xy), cap)
     if n < 0:
         raise RuntimeError(f"oracle_run failed ({n})")
     out = RunResult(off_o, xy_o[:n].copy(), hist, sums, rho, res_off, None)

@@ -338,6 +338,46 @@ void oracle_combine(int32_t G, int32_t H, int32_t W, int32_t r, int32_t passes,
     }
 }
 
+/*
+ * Layer interaction with a general matrix (Eq. 3): rho_l = sum_b M(l, b) S_b / s^passes,
+ * M given row-major as G x G doubles (Sec. 3.2: ordinal, modular or nominal bins can
+ * use other matrices than Eq. 4's).
+ */
+void oracle_combine_matrix(int32_t G, int32_t H, int32_t W, int32_t r, int32_t passes,
+                           const double* M, const int64_t* sums, double* rho) {
+    const int64_t C = (int64_t)H * W;
+    double s = (double)(2 * r + 1) * (double)(2 * r + 1);
+    double sk = 1;
+    for (int32_t p = 0; p < passes; ++p) sk *= s;
+    for (int64_t l = 0; l < G; ++l)
+        for (int64_t c = 0; c < C; ++c) {
+            double acc = 0;
+            for (int64_t b = 0; b < G; ++b) acc += M[l * G + b] * (double)sums[b * C + c];
+            rho[l * C + c] = acc / sk;
+        }
+}
+
+/*
+ * Directed graphs (Sec. 3): interior sample points are translated by `amount`
+ * pixels along the normal of their edge, (-dy, dx) / |d| for the direction d from
+ * source to target, so edges of opposite directions separate. Applied in place
+ * to polylines after their first sampling; endpoints stay.
+ */
+void oracle_directed_offset(int64_t n_edges, const int64_t* off, double* xy, double amount,
+                            int32_t W, int32_t H) {
+    for (int64_t e = 0; e < n_edges; ++e) {
+        int64_t a = off[e], b = off[e + 1] - 1;
+        double dx = xy[2 * b] - xy[2 * a], dy = xy[2 * b + 1] - xy[2 * a + 1];
+        double len = std::sqrt(dx * dx + dy * dy);
+        if (!(len > 0)) continue;
+        double nx = -dy / len, ny = dx / len;
+        for (int64_t k = a + 1; k < b; ++k) {
+            xy[2 * k] = clamp_pos(xy[2 * k] + amount * nx, W);
+            xy[2 * k + 1] = clamp_pos(xy[2 * k + 1] + amount * ny, H);
+        }
+    }
+}
+
 /* Bilinear density and gradient of one layer at n points (xy interleaved). */
 void oracle_density_at(int32_t H, int32_t W, const double* layer, int64_t n, const double* xy,
                        double* rho_out, double* grad_out) {
@@ -371,10 +411,30 @@ double oracle_bandwidth(int32_t iteration, int32_t r, int32_t passes, double h_m
  * `accepted` (nullable) receives, per point, the accepted trial index, -1 when
  * none was accepted and -2 for endpoints.
  */
+void oracle_advect_laplace_mode(int64_t n_edges, const int64_t* off, const double* xy_in,
+                                const int32_t* group, int32_t G, int32_t H, int32_t W,
+                                const double* rho, double h, double eps, int32_t tries,
+                                double beta, int32_t fixed_step, double* xy_out,
+                                int32_t* accepted);
+
 void oracle_advect_laplace(int64_t n_edges, const int64_t* off, const double* xy_in,
                            const int32_t* group, int32_t G, int32_t H, int32_t W,
                            const double* rho, double h, double eps, int32_t tries, double beta,
                            double* xy_out, int32_t* accepted) {
+    oracle_advect_laplace_mode(n_edges, off, xy_in, group, G, H, W, rho, h, eps, tries, beta, 0,
+                               xy_out, accepted);
+}
+
+/*
+ * As oracle_advect_laplace; with fixed_step != 0 every interior point moves by
+ * exactly h along d with no density test: the original KDEEB advection that
+ * Sec. 3.3 and Fig. 3 compare the optimised step against.
+ */
+void oracle_advect_laplace_mode(int64_t n_edges, const int64_t* off, const double* xy_in,
+                                const int32_t* group, int32_t G, int32_t H, int32_t W,
+                                const double* rho, double h, double eps, int32_t tries,
+                                double beta, int32_t fixed_step, double* xy_out,
+                                int32_t* accepted) {
     (void)G;
     const int64_t C = (int64_t)H * W;
     std::vector<double> A;
@@ -391,6 +451,12 @@ void oracle_advect_laplace(int64_t n_edges, const int64_t* off, const double* xy
             bilinear_gradient(layer, H, W, x, y, &gx, &gy);
             double den = std::max(std::sqrt(gx * gx + gy * gy), eps);
             double dx = gx / den, dy = gy / den;
+            if (fixed_step) {
+                A[2 * j] = clamp_pos(x + h * dx, W);
+                A[2 * j + 1] = clamp_pos(y + h * dy, H);
+                if (accepted) accepted[off[e] + j] = 0;
+                continue;
+            }
             double r0 = bilinear_density(layer, H, W, x, y);
             for (int32_t t = 0; t < tries; ++t) {
                 double m = std::ldexp(h, -t);
@@ -425,12 +491,42 @@ void oracle_advect_laplace(int64_t n_edges, const int64_t* off, const double* xy
  * Returns the number of output points, or a negative error:
  * -1 capacity, -2 degenerate polyline, -3 smoothing overflow / radius.
  */
+int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy_in,
+                        const int32_t* group, const int32_t* weight, int32_t G, int32_t H,
+                        int32_t W, int32_t r, int32_t passes, int32_t alpha_num, int32_t alpha_den,
+                        double h_max_sigmas, double lambda, int32_t n_fixed, int32_t n_max,
+                        double delta, double beta, double eps, int32_t tries, int32_t iter0,
+                        int32_t n_iters, int32_t fixed_step, double directed_offset,
+                        const double* M, int64_t* off_out, double* xy_out, int64_t cap,
+                        int64_t* last_hist, int64_t* last_sums, double* last_rho,
+                        int64_t* last_res_off, double* last_res_xy, int64_t res_cap);
+
 int64_t oracle_run(int64_t n_edges, const int64_t* off_in, const double* xy_in,
                    const int32_t* group, const int32_t* weight, int32_t G, int32_t H, int32_t W,
                    int32_t r, int32_t passes, int32_t alpha_num, int32_t alpha_den,
                    double h_max_sigmas, double lambda, int32_t n_fixed, int32_t n_max,
                    double delta, double beta, double eps, int32_t tries, int32_t iter0,
                    int32_t n_iters, int64_t* off_out, double* xy_out, int64_t cap,
+                   int64_t* last_hist, int64_t* last_sums, double* last_rho,
+                   int64_t* last_res_off, double* last_res_xy, int64_t res_cap) {
+    return oracle_run_mode(n_edges, off_in, xy_in, group, weight, G, H, W, r, passes, alpha_num,
+                           alpha_den, h_max_sigmas, lambda, n_fixed, n_max, delta, beta, eps,
+                           tries, iter0, n_iters, 0, 0.0, nullptr, off_out, xy_out, cap,
+                           last_hist, last_sums, last_rho, last_res_off, last_res_xy, res_cap);
+}
+
+/*
+ * The loop with its variants: fixed_step (KDEEB step, Sec. 3.3), directed_offset
+ * (pixels, applied after the first sampling of iteration 0, Sec. 3) and M (a G x G
+ * interaction matrix replacing Eq. 4's; NULL keeps Eq. 4 with alpha).
+ */
+int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy_in,
+                   const int32_t* group, const int32_t* weight, int32_t G, int32_t H, int32_t W,
+                   int32_t r, int32_t passes, int32_t alpha_num, int32_t alpha_den,
+                   double h_max_sigmas, double lambda, int32_t n_fixed, int32_t n_max,
+                   double delta, double beta, double eps, int32_t tries, int32_t iter0,
+                   int32_t n_iters, int32_t fixed_step, double directed_offset,
+                   const double* M, int64_t* off_out, double* xy_out, int64_t cap,
                    int64_t* last_hist, int64_t* last_sums, double* last_rho,
                    int64_t* last_res_off, double* last_res_xy, int64_t res_cap) {
     const int64_t C = (int64_t)H * W;
@@ -445,13 +541,19 @@ int64_t oracle_run(int64_t n_edges, const int64_t* off_in, const double* xy_in,
         int64_t n = oracle_resample(n_edges, P_off.data(), P_xy.data(), n_fixed, n_max, delta,
                                     R_off.data(), R_xy.data(), pts_cap);
         if (n < 0) return n;
+        if (directed_offset != 0 && iter0 + it == 0)
+            oracle_directed_offset(n_edges, R_off.data(), R_xy.data(), directed_offset, W, H);
         oracle_splat(n_edges, R_off.data(), R_xy.data(), group, weight, G, H, W, hist.data());
         if (oracle_smooth(G, H, W, r, passes, hist.data(), sums.data()) != 0) return -3;
-        oracle_combine(G, H, W, r, passes, alpha_num, alpha_den, sums.data(), rho.data());
+        if (M)
+            oracle_combine_matrix(G, H, W, r, passes, M, sums.data(), rho.data());
+        else
+            oracle_combine(G, H, W, r, passes, alpha_num, alpha_den, sums.data(), rho.data());
         double h = oracle_bandwidth(iter0 + it, r, passes, h_max_sigmas, lambda);
         P_xy.assign((size_t)(2 * n), 0.0);
-        oracle_advect_laplace(n_edges, R_off.data(), R_xy.data(), group, G, H, W, rho.data(), h,
-                              eps, tries, beta, P_xy.data(), nullptr);
+        oracle_advect_laplace_mode(n_edges, R_off.data(), R_xy.data(), group, G, H, W,
+                                   rho.data(), h, eps, tries, beta, fixed_step, P_xy.data(),
+                                   nullptr);
         P_off = R_off;
     }
     int64_t n = P_off[(size_t)n_edges];

@@ -373,3 +373,55 @@ def test_run_single_edge_on_centre_row_stays(oracle_mod):
     prm = oracle_mod.Params(radius=2, passes=3, n_fixed=12)
     r = oracle_mod.run(off, xy, None, None, 1, H, W, prm, n_iters=4)
     np.testing.assert_allclose(r.xy[:, 1], 16.5, atol=1e-12)
+
+
+# ----------------------------------------------------------------- variants (Sec. 3, Sec. 3.2, Sec. 3.3)
+def test_fixed_step_moves_by_h_even_downhill(oracle_mod):
+    # KDEEB's step (Sec. 3.3, Fig. 3): magnitude h, no density test -- on the quadratic
+    # bump a point 0.2 px below the peak with h = 4 overshoots to a lower density
+    H, W, c = 8, 32, 15
+    b, a = np.mgrid[0:H, 0:W]
+    rho = (-((a - c) ** 2)).astype(np.float64)[None]
+    px = c - 0.2 + 0.5
+    off = np.array([0, 3], np.int64)
+    xy = np.array([[2.0, 4.0], [px, 4.5], [30.0, 4.0]])
+    out, acc = oracle_mod.advect_laplace(off, xy, [0], rho, 4.0, beta=0.0, fixed_step=True)
+    np.testing.assert_allclose(out[1], [px + 4.0, 4.5], atol=1e-12)
+    r0, _ = oracle_mod.density_at(rho[0], xy[1:2])
+    r1, _ = oracle_mod.density_at(rho[0], out[1:2])
+    assert r1[0] < r0[0]
+    opt, _ = oracle_mod.advect_laplace(off, xy, [0], rho, 4.0, beta=0.0)
+    assert abs(opt[1, 0] - px) < 0.5  # the optimised step only takes a small, uphill move
+
+
+def test_combine_matrix_routes_agree(oracle_mod):
+    rng = np.random.default_rng(21)
+    r, k = 2, 3
+    sk = float((2 * r + 1) ** (2 * k))
+    S = rng.integers(0, 10**8, (3, 5, 6)).astype(np.int64)
+    np.testing.assert_allclose(oracle_mod.combine_matrix(S, r, k, np.eye(3)), S / sk, rtol=1e-15)
+    # Eq. 4 as a matrix equals the alpha form
+    alpha = 0.25
+    M = np.full((3, 3), -alpha / 2)
+    np.fill_diagonal(M, 1.0)
+    np.testing.assert_allclose(oracle_mod.combine_matrix(S, r, k, M),
+                               oracle_mod.combine(S, r, k, 1, 4), rtol=1e-12)
+    # an ordinal interaction (neighbouring bins attract half as much) on two groups
+    Mo = np.array([[1.0, 0.5], [0.5, 1.0]])
+    rho = oracle_mod.combine_matrix(S[:2], r, k, Mo)
+    np.testing.assert_allclose(rho[0], (S[0] + 0.5 * S[1]) / sk, rtol=1e-12)
+
+
+def test_directed_offset_separates_opposite_edges(oracle_mod):
+    # Sec. 3: interior points move along the normal (-dy, dx)/|d| of their edge, so the
+    # same segment drawn in opposite directions splits into two lines 2 * amount apart
+    off, xy = oracle_mod.straight_polylines([[10.0, 20.0], [50.0, 20.0]],
+                                            [[50.0, 20.0], [10.0, 20.0]])
+    r_off, r_xy = oracle_mod.resample(off, xy, n_fixed=9)
+    moved = oracle_mod.directed_offset(r_off, r_xy, 0.75, 64, 48)
+    a, b = moved[r_off[0]:r_off[1]], moved[r_off[1]:r_off[2]]
+    np.testing.assert_allclose(a[1:-1, 1], 20.75)
+    np.testing.assert_allclose(b[1:-1, 1], 19.25)
+    np.testing.assert_array_equal(a[[0, -1]], r_xy[[0, 8]])
+    np.testing.assert_array_equal(b[[0, -1]], r_xy[[9, 17]])
+    np.testing.assert_allclose(a[1:-1, 0], r_xy[1:8, 0])
