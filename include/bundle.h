@@ -70,8 +70,15 @@ typedef struct {
     int32_t step_tries;       /* step sizes tried: h, h/2, ..., h/2^(tries-1) (Sec. 3.3) */
     int32_t sum_bits;         /* width of the smoothed sums: 0 auto, 32 or 64 */
     int32_t rho_dtype;        /* bundle_rho_dtype */
-    int32_t flags;            /* reserved, 0 */
+    int32_t flags;            /* BUNDLE_FLAG_* */
+    float directed_offset;    /* directed graphs (Sec. 3): after the first sampling, interior
+                                 points move this fraction of max(W, H) along the normal
+                                 (-dy, dx)/|d| of their edge; 0 = off (paper: 0.001..0.005) */
 } bundle_params;
+
+/* bundle_params.flags */
+#define BUNDLE_FLAG_FIXED_STEP 1 /* KDEEB's advection (Sec. 3.3, Fig. 3): step exactly h, no
+                                    density test -- the baseline the optimised step improves */
 
 /* Result of bundle_get_info. */
 typedef struct {
@@ -199,6 +206,16 @@ int32_t bundle_batch_size(const bundle_ctx* ctx);
  * batch is destroyed: bundle_fetch, bundle_fetch_density and bundle_get_info work
  * on it; bundle_iterate on a member returns ESTATE, bundle_destroy ignores it. */
 bundle_ctx* bundle_batch_member(bundle_ctx* ctx, int32_t k);
+
+/*
+ * General layer interaction (Eq. 3): replace Eq. 4's matrix by
+ * M(l, b) = num[l * G + b] / den (row-major G x G, den > 0), e.g. for ordinal or
+ * modular bins (Sec. 3.2). The mix stays exact: rho_l = (sum_b num[l,b] S_b) /
+ * (den s^k) with an int64 numerator. Returns EOVERFLOW when
+ * max_l sum_b |num[l,b]| times the smoothed-sum bound does not fit int64, EINVAL
+ * for den <= 0 or a batch context. num is copied; applies from the next iteration.
+ */
+bundle_status bundle_set_interaction(bundle_ctx* ctx, const int64_t* num, int64_t den);
 
 /* Sizes, widths, map, schedule and point counts of a context (synchronises the stream).
  * For a batch: sums of the counts over its graphs; sizes and map of graph 0. */

@@ -24,6 +24,7 @@ BUNDLE_OK, BUNDLE_EINVAL, BUNDLE_ENOMEM, BUNDLE_ECUDA = 0, 1, 2, 3
 BUNDLE_EOVERFLOW, BUNDLE_ETIMEOUT, BUNDLE_ESTATE, BUNDLE_ENOTSUP = 4, 5, 6, 7
 RHO_F32, RHO_BF16, RHO_F16 = 0, 1, 2
 INPUT_DEVICE = 1
+FLAG_FIXED_STEP = 1
 FETCH_DEVICE, FETCH_PIXELS, FETCH_RESAMPLED = 1, 2, 4
 DENSITY_HIST, DENSITY_SUMS, DENSITY_RHO = 0, 1, 2
 PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "combine",
@@ -33,7 +34,8 @@ EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bu
             "bundle_fetch", "bundle_fetch_density", "bundle_get_info", "bundle_sync",
             "bundle_destroy", "bundle_last_error", "bundle_status_string",
             "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc",
-            "bundle_init_batch", "bundle_batch_size", "bundle_batch_member")
+            "bundle_init_batch", "bundle_batch_size", "bundle_batch_member",
+            "bundle_set_interaction")
 
 
 class BundleParams(ctypes.Structure):
@@ -48,6 +50,7 @@ class BundleParams(ctypes.Structure):
         ("delta_px", ctypes.c_float), ("laplace_beta", ctypes.c_float), ("eps", ctypes.c_float),
         ("step_tries", ctypes.c_int32), ("sum_bits", ctypes.c_int32),
         ("rho_dtype", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("directed_offset", ctypes.c_float),
     ]
 
 
@@ -127,6 +130,8 @@ def lib():
     L.bundle_batch_size.restype = i32
     L.bundle_batch_member.argtypes = [P, i32]
     L.bundle_batch_member.restype = P
+    L.bundle_set_interaction.argtypes = [P, P, i64]
+    L.bundle_set_interaction.restype = i32
     _lib = L
     return L
 
@@ -250,6 +255,12 @@ def bundle_batch_member(ctx, k: int):
     if not h:
         raise IndexError(k)
     return ctypes.c_void_p(h)
+
+
+def bundle_set_interaction(ctx, num, den: int):
+    """General interaction matrix M = num / den (G x G integers, Eq. 3)."""
+    n = np.ascontiguousarray(num, dtype=np.int64)
+    _check(lib().bundle_set_interaction(ctx, _ptr(n), int(den)), ctx)
 
 
 def bundle_iterate(ctx, n_iters: int):

@@ -27,6 +27,8 @@ struct bundle_ctx {
     int32_t sum_bits = 64;
     int64_t mix_self = 1, mix_all = 0;
     float den_f = 1.0f;
+    double sum_bound = 0;        // worst-case smoothed sum (size_integers)
+    int64_t* mix = nullptr;      // optional G x G interaction numerators (device)
     double map[5] = {0, 0, 1, 0, 0};
     int32_t iteration = 0;
     int device = 0;
@@ -137,7 +139,7 @@ void free_ctx(bundle_ctx* c) {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->perm, c->group, c->weight, c->cnt[0], c->cnt[1], c->pts[0], c->pts[1],
-                    c->hist, c->Y, c->S, c->rho, c->quads, c->counters, c->fetch_off, c->fetch_tmp,
+                    c->hist, c->Y, c->S, c->rho, c->quads, c->mix, c->counters, c->fetch_off, c->fetch_tmp,
                     c->fetch_xy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -192,6 +194,10 @@ bundle_status check_params(const bundle_params& p, int32_t n_groups, std::string
     if (p.rho_dtype < 0 || p.rho_dtype > 2) return fail(e, BUNDLE_EINVAL, "bad rho_dtype");
     if (p.grid_dominant < 2 || p.grid_dominant > 4096)
         return fail(e, BUNDLE_EINVAL, "grid_dominant must be in [2, 4096]");
+    if ((p.flags & ~BUNDLE_FLAG_FIXED_STEP) != 0)
+        return fail(e, BUNDLE_EINVAL, "unknown bits in flags");
+    if (!(p.directed_offset >= 0 && p.directed_offset < 0.25f))
+        return fail(e, BUNDLE_EINVAL, "directed_offset must be in [0, 0.25)");
     return BUNDLE_OK;
 }
 
@@ -226,6 +232,7 @@ bundle_status size_integers(bundle_ctx* c, const int32_t* weight_host, std::stri
     if (!(bound < two63 * (1 - 1e-12)))
         return fail(e, BUNDLE_EOVERFLOW, "smoothed-sum bound %.6g does not fit int64", bound);
     c->sum_bits = bits;
+    c->sum_bound = bound;
     double sk = 1;
     for (int p = 0; p < c->p.passes; ++p) sk *= s;
     if (c->G > 1) {
@@ -504,6 +511,11 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
     a.n_fixed = c->p.n_fixed;
     a.n_max = c->p.n_max;
     a.delta = c->p.delta_px;
+    a.fixed_step = (c->p.flags & BUNDLE_FLAG_FIXED_STEP) ? 1 : 0;
+    // the directed offset applies to the first sampling of the run only
+    a.dir_amount = (mode == kModeResample && c->iteration == 0)
+                       ? (float)((double)c->p.directed_offset * std::max(c->W, c->H))
+                       : 0.0f;
     if (mode & kModeResample)
         CUDA_TRY(&c->err, timed(c, kProfHistClear, [&] {
                      return cudaMemsetAsync(c->hist, 0,
@@ -529,6 +541,7 @@ bundle_status run_filter(bundle_ctx* c) {
     f.W = c->W;
     f.r = c->p.radius;
     f.passes = c->p.passes;
+    f.mix = c->mix;
     f.mix_self = c->mix_self;
     f.mix_all = c->mix_all;
     f.den_f = c->den_f;
@@ -1182,6 +1195,38 @@ bundle_status bundle_get_info(const bundle_ctx* c, bundle_info* out) {
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return BUNDLE_ECUDA;
     out->points_processed = (int64_t)done;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_set_interaction(bundle_ctx* c, const int64_t* num, int64_t den) {
+    if (!c) return BUNDLE_EINVAL;
+    if (!c->members.empty() || c->is_member)
+        return fail(&c->err, BUNDLE_EINVAL, "the interaction matrix applies to single-graph contexts");
+    if (!num || den <= 0) return fail(&c->err, BUNDLE_EINVAL, "need num and den > 0");
+    const int G = c->G;
+    double worst = 0;
+    for (int l = 0; l < G; ++l) {
+        double row = 0;
+        for (int b = 0; b < G; ++b) row += std::fabs((double)num[l * G + b]);
+        worst = std::max(worst, row);
+    }
+    if (!(worst * c->sum_bound < 9223372036854775808.0 * (1 - 1e-12)))
+        return fail(&c->err, BUNDLE_EOVERFLOW,
+                    "interaction bound %.6g x %.6g does not fit int64", worst, c->sum_bound);
+    double sk = 1;
+    const double s = (double)(2 * c->p.radius + 1) * (double)(2 * c->p.radius + 1);
+    for (int p = 0; p < c->p.passes; ++p) sk *= s;
+    DeviceGuard dg(c->device);
+    if (!c->mix) CUDA_TRY(&c->err, dalloc(c, &c->mix, (size_t)G * G));
+    CUDA_TRY(&c->err, cudaMemcpyAsync(c->mix, num, (size_t)G * G * sizeof(int64_t),
+                                      cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    c->den_f = (float)((double)den * sk);
+    for (cudaGraphExec_t& g : c->gexec)  // captured with the previous mix
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     return BUNDLE_OK;
 }
 

@@ -54,6 +54,8 @@ struct StepArgs {
     float lap_half_beta;     // beta / 2
     int32_t n_fixed, n_max;
     float delta;
+    int32_t fixed_step;      // KDEEB step: exactly h, no density test
+    float dir_amount;        // directed graphs: normal offset (px) of interior resampled points
 };
 
 struct FilterArgs {
@@ -64,6 +66,7 @@ struct FilterArgs {
     void* rho;             // [G][H][W] density (rho type)
     void* quads;           // [G][H+3][W+3] density quads (rho type x 4)
     int32_t G, H, W, r, passes;
+    const int64_t* mix;    // optional G x G integer interaction numerators (row-major)
     int64_t mix_self;      // q (G - 1) + p : weight of a group's own layer
     int64_t mix_all;       // p : weight of the all-groups sum
     float inv_den_f;       // unused (kept for a future reciprocal form)

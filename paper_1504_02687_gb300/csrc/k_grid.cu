@@ -361,8 +361,32 @@ cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
     return colbox_strip<TS, 2>(a, st);
 }
 
+// General interaction (Eq. 3): rho_l = (sum_b num[l, b] S_b) / (den s^k), exact int64
+// numerator; the matrix is staged in shared memory once per CTA.
+template <typename TS, typename R>
+__global__ void k_combine_matrix(const TS* __restrict__ S, R* __restrict__ rho, int G, int64_t C,
+                                 const int64_t* __restrict__ num, float den) {
+    extern __shared__ long long s_num[];
+    for (int k = threadIdx.x; k < G * G; k += blockDim.x) s_num[k] = num[k];
+    __syncthreads();
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= C) return;
+    for (int l = 0; l < G; ++l) {
+        long long acc = 0;
+        for (int b = 0; b < G; ++b) acc += s_num[l * G + b] * (long long)S[(size_t)b * C + idx];
+        rho[(size_t)l * C + idx] = to_rho<R>(__fdiv_rn(__ll2float_rn(acc), den));
+    }
+}
+
 template <typename TS, typename R>
 cudaError_t combine_t(const FilterArgs& a, cudaStream_t st) {
+    if (a.mix) {
+        const int64_t C = (int64_t)a.H * a.W;
+        k_combine_matrix<TS, R><<<(unsigned)((C + 255) / 256), 256,
+                                  (size_t)a.G * a.G * sizeof(long long), st>>>(
+            static_cast<const TS*>(a.S), static_cast<R*>(a.rho), a.G, C, a.mix, a.den_f);
+        return cudaGetLastError();
+    }
     const int64_t C = (int64_t)a.H * a.W;
     k_combine<TS, R><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(
         static_cast<const TS*>(a.S), static_cast<R*>(a.rho), a.G, C, a.mix_self, a.mix_all,

@@ -76,7 +76,7 @@ __device__ __forceinline__ float clamp_pos(float v, int n) {
 // starts at h and halves until the density is not lower than at x.
 template <typename T>
 __device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, float h,
-                               float eps, int tries) {
+                               float eps, int tries, int fixed_step) {
     Frame f = frame_of(p.x, p.y, W, H);
     const int64_t Wq = W + kQuadPad;
     const int64_t c = (int64_t)(f.b0 + 2) * Wq + (f.a0 + 2);
@@ -99,6 +99,8 @@ __device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, 
     const float n2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
     const float inv = n2 > eps * eps ? rsqrtf(n2) : __frcp_rn(eps);
     const float dx = __fmul_rn(gx, inv), dy = __fmul_rn(gy, inv);
+    if (fixed_step)  // KDEEB's step (Sec. 3.3): magnitude h whatever the density there
+        return make_float2(clamp_pos(__fmaf_rn(h, dx, p.x), W), clamp_pos(__fmaf_rn(h, dy, p.y), H));
     float m = h;
     for (int t = 0; t < tries; ++t) {
         float xn = clamp_pos(__fmaf_rn(m, dx, p.x), W);
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                 const int j = p0 + k - s_loc[i];
                 if (j > 0 && j < s_cnt[i] - 1) {
                     const T* Q = static_cast<const T*>(a.quads) + (int64_t)s_grp[i] * QC * 4;
-                    s_pts[k] = advect_point(s_pts[k], Q, a.W, a.H, h, a.eps, a.tries);
+                    s_pts[k] = advect_point(s_pts[k], Q, a.W, a.H, h, a.eps, a.tries, a.fixed_step);
                 }
             }
             __syncthreads();
@@ -316,6 +318,17 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                 const int64_t ob = region + out_base + s_locn[i];
                 const int g = s_grp[i], w = s_w[i];
                 uint32_t* hl = a.hist + hist_copy * a.G * (size_t)a.W * a.H + (size_t)g * a.W * a.H;
+                // directed graphs (Sec. 3): interior points shift along the edge normal
+                float ox = 0.0f, oy = 0.0f;
+                if (a.dir_amount != 0.0f) {
+                    const float2 P0 = s_pts[q], P1 = s_pts[q + n - 1];
+                    const float ddx = __fsub_rn(P1.x, P0.x), ddy = __fsub_rn(P1.y, P0.y);
+                    const float len = sqrtf(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)));
+                    if (len > 0.0f) {
+                        ox = -a.dir_amount * ddy / len;
+                        oy = a.dir_amount * ddx / len;
+                    }
+                }
                 // endpoints are copied; an edge of zero length puts every point on its source
                 for (int j = lane; j < m; j += 32) {
                     if (j == m - 1) emit(a, hl, ob + j, s_pts[q + n - 1], w);
@@ -336,8 +349,11 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                         float fr = seg > 0.0f ? __fdividef(__fsub_rn(t, c0), seg) : 0.0f;
                         fr = fminf(fmaxf(fr, 0.0f), 1.0f);
                         const float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
-                        emit(a, hl, ob + j,
-                             make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr)), w);
+                        float2 R = make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr));
+                        if (ox != 0.0f || oy != 0.0f)
+                            R = make_float2(clamp_pos(__fadd_rn(R.x, ox), a.W),
+                                            clamp_pos(__fadd_rn(R.y, oy), a.H));
+                        emit(a, hl, ob + j, R, w);
                     }
                 }
                 if (lane == 0) a.cnt_out[e0 + i] = m;

@@ -74,8 +74,9 @@ def advect_mismatch(off, R, group, rho, h, p, gpu_P, tol):
     small for its direction to be resolved in FP32 (|g| <= 1e-4 |rho|), or a step test with
     |rho(x'_t) - rho(x)| within 1e-5 of the densities for a trial t up to the accepted one.
     """
+    fixed = bool(p.flags & pkg.FLAG_FIXED_STEP)
     P_o, acc = oracle.advect_laplace(off, R, group, rho, h, eps=float(p.eps), tries=p.step_tries,
-                                     beta=float(p.laplace_beta))
+                                     beta=float(p.laplace_beta), fixed_step=fixed)
     err = np.hypot(*(gpu_P - P_o).T)
     bad = np.flatnonzero(err > tol)
     if len(bad) == 0:
@@ -100,6 +101,8 @@ def advect_mismatch(off, R, group, rho, h, p, gpu_P, tol):
         if gn <= 1e-4 * abs(r0[0]) + 1e-30:
             amb[q] = True
             continue
+        if fixed:  # no step test: only the direction can be ambiguous
+            continue
         d = g[0] / max(gn, float(p.eps))
         last = acc[q] if acc[q] >= 0 else p.step_tries - 1
         for t in range(last + 1):
@@ -119,10 +122,13 @@ def advect_mismatch(off, R, group, rho, h, p, gpu_P, tol):
     return len(bad), unexplained, P_o
 
 
-def resample_mismatch(off_in, P, off_gpu, R_gpu, p, tol):
+def resample_mismatch(off_in, P, off_gpu, R_gpu, p, tol, directed_px=0.0, grid=None):
     """Oracle resampling of the GPU's polylines vs the GPU's. A count that differs must come
-    from an arc length within FP32 rounding of a multiple of delta (by-length mode only)."""
+    from an arc length within FP32 rounding of a multiple of delta (by-length mode only).
+    directed_px: the directed-graph normal offset of the first sampling (Sec. 3)."""
     o_off, o_R = oracle.resample(off_in, P, p.n_fixed, p.n_max, float(p.delta_px))
+    if directed_px:
+        o_R = oracle.directed_offset(o_off, o_R, directed_px, grid[0], grid[1])
     cg, co = np.diff(off_gpu), np.diff(o_off)
     diff_cnt = np.flatnonzero(cg != co)
     unexplained = 0

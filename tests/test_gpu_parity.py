@@ -69,7 +69,7 @@ def test_grid_map_matches_oracle_bit_for_bit():
         pkg.bundle_destroy(ctx)
 
 
-def _lockstep_once(ctx, w, p, max_bad_frac=1e-3):
+def _lockstep_once(ctx, w, p, max_bad_frac=1e-3, M=None):
     """One GPU iteration from the GPU's current state, every stage checked against the oracle."""
     info = pkg.bundle_get_info(ctx)
     it = info.iteration
@@ -83,7 +83,8 @@ def _lockstep_once(ctx, w, p, max_bad_frac=1e-3):
     G, H, W = hist.shape
     extent = max(W, H)
     # resampling (Sec. 2.1): counts exact up to verified ties, positions to FP32 rounding
-    n_cnt, n_cnt_bad, worst = resample_mismatch(off0, P0, offR, R, p, 0)
+    dpx = float(p.directed_offset) * extent if it == 0 else 0.0
+    n_cnt, n_cnt_bad, worst = resample_mismatch(off0, P0, offR, R, p, 0, dpx, (W, H))
     assert n_cnt_bad == 0
     # FP32 arc-length sums: a few ulps of the extent per point of the polyline
     assert worst <= 8 * max(p.n_fixed, p.n_max) * 2.0 ** -23 * extent, worst
@@ -94,7 +95,10 @@ def _lockstep_once(ctx, w, p, max_bad_frac=1e-3):
     # box passes (Sec. 3.1): bit for bit
     np.testing.assert_array_equal(S, oracle.smooth(hist, p.radius, p.passes))
     # layer mix (Eq. 3, Eq. 4): exact integer numerator, one FP32 rounding and division
-    rho_o = oracle.combine(S, p.radius, p.passes, p.alpha_num, p.alpha_den)
+    if M is None:
+        rho_o = oracle.combine(S, p.radius, p.passes, p.alpha_num, p.alpha_den)
+    else:
+        rho_o = oracle.combine_matrix(S, p.radius, p.passes, M)
     rel, absl = {pkg.RHO_F32: (2.0 ** -21, 1e-35), pkg.RHO_BF16: (2.0 ** -8, 1e-35),
                  pkg.RHO_F16: (2.0 ** -10, 2.0 ** -24)}[info.rho_dtype]
     np.testing.assert_array_less(np.abs(rho - rho_o), rel * np.abs(rho_o) + absl)
@@ -277,6 +281,67 @@ def test_device_inputs_and_outputs():
     finally:
         pkg.bundle_destroy(ctx_h)
         pkg.bundle_destroy(ctx_d)
+
+
+def test_variants_fixed_step_directed_offset():
+    """KDEEB's fixed step (Sec. 3.3) and the directed-graph normal offset (Sec. 3), checked
+    stage by stage against the oracle's variants."""
+    for over in (dict(flags=pkg.FLAG_FIXED_STEP), dict(directed_offset=0.004)):
+        w, p, ctx = _make("g3-bylength-weighted", **over)
+        try:
+            _lockstep_once(ctx, w, p)
+            _lockstep_once(ctx, w, p)
+        finally:
+            pkg.bundle_destroy(ctx)
+
+
+def test_optimised_step_never_lowers_density():
+    """Sec. 3.3: the halving step guarantees every advected point a density not lower than
+    before; KDEEB's fixed step does not (beta = 0 so the advected points are the output)."""
+    dec = {}
+    for flags in (0, pkg.FLAG_FIXED_STEP):
+        w, p, ctx = _make("g1-fixed32", laplace_beta=0.0, flags=flags)
+        try:
+            pkg.bundle_iterate(ctx, 2)
+            pkg.bundle_iterate(ctx, 1)
+            offR, R = fetch_px(ctx, resampled=True)
+            rho = rho_as_f64(ctx)
+            off1, P1 = fetch_px(ctx)
+        finally:
+            pkg.bundle_destroy(ctx)
+        r0, _ = oracle.density_at(rho[0], R)
+        r1, _ = oracle.density_at(rho[0], P1)
+        interior = np.ones(len(R), bool)
+        interior[offR[:-1]] = False
+        interior[offR[1:] - 1] = False
+        drop = (r1 < r0 - 1e-5 * np.abs(r0) - 1e-30) & interior
+        dec[flags] = int(drop.sum())
+    assert dec[0] == 0
+    assert dec[pkg.FLAG_FIXED_STEP] > 0
+
+
+def test_interaction_matrix():
+    """Eq. 4 written as a general matrix reproduces the default mix bit for bit; an ordinal
+    matrix (Sec. 3.2) is checked against the oracle's matrix mix."""
+    w, p, ctx = _make("g3-bylength-weighted")
+    w2, p2, ctx2 = _make("g3-bylength-weighted")
+    try:
+        G = w.n_groups
+        num = np.full((G, G), -1, np.int64)  # alpha = 1/4, B - 1 = 2: -1/8 off the diagonal
+        np.fill_diagonal(num, 8)
+        pkg.bundle_set_interaction(ctx2, num, 8)
+        pkg.bundle_iterate(ctx, 3)
+        pkg.bundle_iterate(ctx2, 3)
+        np.testing.assert_array_equal(pkg.bundle_fetch_density(ctx, pkg.DENSITY_RHO),
+                                      pkg.bundle_fetch_density(ctx2, pkg.DENSITY_RHO))
+        np.testing.assert_array_equal(pkg.bundle_fetch(ctx, pixels=True)[1],
+                                      pkg.bundle_fetch(ctx2, pixels=True)[1])
+        ordinal = np.array([[4, 2, -1], [2, 4, 2], [-1, 2, 4]], np.int64)
+        pkg.bundle_set_interaction(ctx2, ordinal, 4)
+        _lockstep_once(ctx2, w2, p2, M=ordinal / 4.0)
+    finally:
+        pkg.bundle_destroy(ctx)
+        pkg.bundle_destroy(ctx2)
 
 
 def test_graph_path_equals_separate_launches():

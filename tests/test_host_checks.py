@@ -37,6 +37,8 @@ def _edges(E, seed=0):
     (dict(grid_w=8192, grid_h=64), "grid"),
     (dict(grid_w=16, grid_h=16, radius=16, margin_px=0), "radius"),
     (dict(grid_w=16, grid_h=16, radius=4, margin_px=8), "margin"),
+    (dict(flags=8), "flags"),
+    (dict(directed_offset=0.5), "directed_offset"),
 ])
 def test_invalid_arguments(pkg, override, needle):
     src, dst = _edges(10)
