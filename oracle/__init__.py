@@ -77,8 +77,10 @@ def _load():
     lib.oracle_directed_offset.argtypes = [i64, P, P, f64, i32, i32]
     lib.oracle_directed_offset.restype = None
     lib.oracle_run_mode.argtypes = ([i64, P, P, P, P, i32, i32, i32, i32, i32, i32, i32, f64, f64,
-                                     i32, i32, f64, f64, f64, i32, i32, i32, i32, f64, P, P, P,
-                                     i64, P, P, P, P, P, i64])
+                                     i32, i32, f64, f64, f64, i32, i32, i32, i32, f64, P, i32, P,
+                                     P, i64, P, P, P, P, P, i64])
+    lib.oracle_splat_segments.argtypes = [i64, P, P, P, P, i32, i32, i32, P]
+    lib.oracle_splat_segments.restype = None
     lib.oracle_run_mode.restype = i64
     _lib = lib
     return lib
@@ -108,6 +110,7 @@ class Params:
     eps: float = 1e-9
     tries: int = 8
     fixed_step: bool = False      # KDEEB step (Sec. 3.3)
+    segment_hist: bool = False    # Bresenham segment histogram (Eq. 1, Sec. 4)
     directed_offset: float = 0.0  # pixels along the edge normal after the first sampling (Sec. 3)
 
 
@@ -163,6 +166,17 @@ def splat(off, xy, group, weight, G, H, W):
     weight = _c(weight, np.int32)
     hist = np.zeros((G, H, W), np.int64)
     lib.oracle_splat(E, _p(off), _p(xy), _p(group), _p(weight), G, H, W, _p(hist))
+    return hist
+
+
+def splat_segments(off, xy, group, weight, G, H, W):
+    """Bresenham segment histogram (Eq. 1 as the paper rasterised it, Sec. 4)."""
+    lib = _load()
+    off = _c(off, np.int64)
+    xy = _c(xy, np.float64).reshape(-1, 2)
+    hist = np.zeros((G, H, W), np.int64)
+    lib.oracle_splat_segments(off.shape[0] - 1, _p(off), _p(xy), _p(_c(group, np.int32)),
+                              _p(_c(weight, np.int32)), G, H, W, _p(hist))
     return hist
 
 
@@ -277,7 +291,8 @@ def run(off, xy, group, weight, G, H, W, prm: Params, iter0=0, n_iters=1, keep_l
                             prm.passes, prm.alpha_num, prm.alpha_den, prm.h_max_sigmas, prm.lam,
                             prm.n_fixed, prm.n_max, prm.delta, prm.beta, prm.eps, prm.tries, iter0,
                             n_iters, 1 if prm.fixed_step else 0, float(prm.directed_offset),
-                            _p(Mc), _p(off_o), _p(xy_o), cap, _p(hist), _p(sums), _p(rho),
+                            _p(Mc), 1 if prm.segment_hist else 0, _p(off_o), _p(xy_o), cap,
+                            _p(hist), _p(sums), _p(rho),
                             _p(res_off), _p(res_xy), cap)
     if n < 0:
         raise RuntimeError(f"oracle_run failed ({n})")

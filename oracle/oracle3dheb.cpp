@@ -264,6 +264,51 @@ void oracle_splat(int64_t n_edges, const int64_t* off, const double* xy, const i
 }
 
 /*
+ * Histogram of edge occurrence by segment rasterisation (Eq. 1 with the paper's
+ * Sec. 4 implementation: Bresenham lines written into the accumulation array).
+ * Each segment P_{j-1} -> P_j of a polyline is walked from the cell of P_{j-1} to
+ * the cell of P_j with the integer Bresenham line algorithm (8-connected, one cell
+ * per step of the major axis), and every cell on the walk gains w_e; the first
+ * cell of segments j >= 2 is the previous segment's last cell and is not counted
+ * again. Cells are floor() of the positions, clamped to the grid.
+ */
+void oracle_splat_segments(int64_t n_edges, const int64_t* off, const double* xy,
+                           const int32_t* group, const int32_t* weight, int32_t G, int32_t H,
+                           int32_t W, int64_t* hist) {
+    std::fill(hist, hist + (int64_t)G * H * W, (int64_t)0);
+    auto cell = [&](double v, int64_t n) {
+        int64_t c = (int64_t)std::floor(v);
+        return std::min<int64_t>(std::max<int64_t>(c, 0), n - 1);
+    };
+    for (int64_t e = 0; e < n_edges; ++e) {
+        int64_t* layer = hist + (int64_t)(group ? group[e] : 0) * H * W;
+        int64_t w = weight ? weight[e] : 1;
+        for (int64_t k = off[e] + 1; k < off[e + 1]; ++k) {
+            int64_t x = cell(xy[2 * (k - 1)], W), y = cell(xy[2 * (k - 1) + 1], H);
+            const int64_t x1 = cell(xy[2 * k], W), y1 = cell(xy[2 * k + 1], H);
+            const int64_t dx = std::llabs(x1 - x), dy = -std::llabs(y1 - y);
+            const int64_t sx = x < x1 ? 1 : -1, sy = y < y1 ? 1 : -1;
+            int64_t err = dx + dy;
+            bool first = true;
+            for (;;) {
+                if (!(first && k > off[e] + 1)) layer[y * W + x] += w;
+                first = false;
+                if (x == x1 && y == y1) break;
+                const int64_t e2 = 2 * err;
+                if (e2 >= dy) {
+                    err += dy;
+                    x += sx;
+                }
+                if (e2 <= dx) {
+                    err += dx;
+                    y += sy;
+                }
+            }
+        }
+    }
+}
+
+/*
  * Density smoothing by repeated averaging filters computed with integral
  * images (Sec. 3.1, after Kovesi's almost-Gaussian filtering and Viola-Jones
  * integral images): `passes` times, each layer X is replaced by its
@@ -497,9 +542,10 @@ int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy
                         double h_max_sigmas, double lambda, int32_t n_fixed, int32_t n_max,
                         double delta, double beta, double eps, int32_t tries, int32_t iter0,
                         int32_t n_iters, int32_t fixed_step, double directed_offset,
-                        const double* M, int64_t* off_out, double* xy_out, int64_t cap,
-                        int64_t* last_hist, int64_t* last_sums, double* last_rho,
-                        int64_t* last_res_off, double* last_res_xy, int64_t res_cap);
+                        const double* M, int32_t segment_hist, int64_t* off_out,
+                        double* xy_out, int64_t cap, int64_t* last_hist, int64_t* last_sums,
+                        double* last_rho, int64_t* last_res_off, double* last_res_xy,
+                        int64_t res_cap);
 
 int64_t oracle_run(int64_t n_edges, const int64_t* off_in, const double* xy_in,
                    const int32_t* group, const int32_t* weight, int32_t G, int32_t H, int32_t W,
@@ -511,14 +557,15 @@ int64_t oracle_run(int64_t n_edges, const int64_t* off_in, const double* xy_in,
                    int64_t* last_res_off, double* last_res_xy, int64_t res_cap) {
     return oracle_run_mode(n_edges, off_in, xy_in, group, weight, G, H, W, r, passes, alpha_num,
                            alpha_den, h_max_sigmas, lambda, n_fixed, n_max, delta, beta, eps,
-                           tries, iter0, n_iters, 0, 0.0, nullptr, off_out, xy_out, cap,
+                           tries, iter0, n_iters, 0, 0.0, nullptr, 0, off_out, xy_out, cap,
                            last_hist, last_sums, last_rho, last_res_off, last_res_xy, res_cap);
 }
 
 /*
  * The loop with its variants: fixed_step (KDEEB step, Sec. 3.3), directed_offset
- * (pixels, applied after the first sampling of iteration 0, Sec. 3) and M (a G x G
- * interaction matrix replacing Eq. 4's; NULL keeps Eq. 4 with alpha).
+ * (pixels, applied after the first sampling of iteration 0, Sec. 3), M (a G x G
+ * interaction matrix replacing Eq. 4's; NULL keeps Eq. 4 with alpha) and
+ * segment_hist (Bresenham segment histogram instead of the point splat).
  */
 int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy_in,
                    const int32_t* group, const int32_t* weight, int32_t G, int32_t H, int32_t W,
@@ -526,7 +573,8 @@ int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy
                    double h_max_sigmas, double lambda, int32_t n_fixed, int32_t n_max,
                    double delta, double beta, double eps, int32_t tries, int32_t iter0,
                    int32_t n_iters, int32_t fixed_step, double directed_offset,
-                   const double* M, int64_t* off_out, double* xy_out, int64_t cap,
+                   const double* M, int32_t segment_hist, int64_t* off_out, double* xy_out,
+                   int64_t cap,
                    int64_t* last_hist, int64_t* last_sums, double* last_rho,
                    int64_t* last_res_off, double* last_res_xy, int64_t res_cap) {
     const int64_t C = (int64_t)H * W;
@@ -543,7 +591,12 @@ int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy
         if (n < 0) return n;
         if (directed_offset != 0 && iter0 + it == 0)
             oracle_directed_offset(n_edges, R_off.data(), R_xy.data(), directed_offset, W, H);
-        oracle_splat(n_edges, R_off.data(), R_xy.data(), group, weight, G, H, W, hist.data());
+        if (segment_hist)
+            oracle_splat_segments(n_edges, R_off.data(), R_xy.data(), group, weight, G, H, W,
+                                  hist.data());
+        else
+            oracle_splat(n_edges, R_off.data(), R_xy.data(), group, weight, G, H, W,
+                         hist.data());
         if (oracle_smooth(G, H, W, r, passes, hist.data(), sums.data()) != 0) return -3;
         if (M)
             oracle_combine_matrix(G, H, W, r, passes, M, sums.data(), rho.data());

@@ -425,3 +425,38 @@ def test_directed_offset_separates_opposite_edges(oracle_mod):
     np.testing.assert_array_equal(a[[0, -1]], r_xy[[0, 8]])
     np.testing.assert_array_equal(b[[0, -1]], r_xy[[9, 17]])
     np.testing.assert_allclose(a[1:-1, 0], r_xy[1:8, 0])
+
+
+# ----------------------------------------------------------------- segment histogram (Eq. 1, Sec. 4)
+def _cells(hist):
+    return sorted(zip(*np.nonzero(hist[0])))
+
+
+def test_segment_histogram_hand_enumerated(oracle_mod):
+    H, W = 12, 16
+    # horizontal, vertical and 45-degree segments: every cell between the end cells
+    for a, b, cells in [((1.5, 2.5), (6.2, 2.9), [(2, x) for x in range(1, 7)]),
+                        ((3.1, 9.9), (3.7, 4.0), [(y, 3) for y in range(4, 10)]),
+                        ((0.5, 0.5), (4.5, 4.5), [(i, i) for i in range(5)])]:
+        off, xy = oracle_mod.straight_polylines([a], [b])
+        assert _cells(oracle_mod.splat_segments(off, xy, None, None, 1, H, W)) == cells
+    # a shallow line: one cell per column (the major axis), rows from the Bresenham rule
+    off, xy = oracle_mod.straight_polylines([[0.5, 0.5]], [[8.5, 3.5]])
+    hist = oracle_mod.splat_segments(off, xy, None, None, 1, H, W)
+    assert hist.sum() == 9 and (hist[0].sum(0)[:9] == 1).all()
+    assert _cells(hist)[0] == (0, 0) and _cells(hist)[-1] == (3, 8)
+
+
+def test_segment_histogram_joints_and_weights(oracle_mod):
+    # an L-shaped polyline: the corner cell is the joint of two segments and counts once;
+    # a zero-length segment (both points in one cell) adds nothing
+    off = np.array([0, 4], np.int64)
+    xy = np.array([[1.2, 1.2], [5.7, 1.4], [5.9, 1.9], [5.5, 6.1]])
+    hist = oracle_mod.splat_segments(off, xy, None, np.array([3], np.int32), 1, 8, 8)
+    expect = {(1, x) for x in range(1, 6)} | {(y, 5) for y in range(1, 7)}
+    assert set(_cells(hist)) == expect
+    assert (hist[hist > 0] == 3).all() and hist.sum() == 3 * len(expect)
+    # a polyline whose points are all in one cell counts that cell once
+    off = np.array([0, 3], np.int64)
+    xy = np.array([[2.1, 2.1], [2.5, 2.9], [2.9, 2.2]])
+    assert oracle_mod.splat_segments(off, xy, None, None, 1, 8, 8).sum() == 1
