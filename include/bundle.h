@@ -79,6 +79,16 @@ typedef struct {
 /* bundle_params.flags */
 #define BUNDLE_FLAG_FIXED_STEP 1 /* KDEEB's advection (Sec. 3.3, Fig. 3): step exactly h, no
                                     density test -- the baseline the optimised step improves */
+#define BUNDLE_FLAG_SEGMENT_HIST 2 /* histogram by Bresenham segments (Eq. 1 as rasterised in
+                                      Sec. 4): every cell on a polyline segment gains w_e, joints
+                                      counted once; default: every sample point adds w_e to its
+                                      cell. The sums' int64 bound is then checked on the device
+                                      each iteration; exceeding it makes the next sync, fetch or
+                                      info call return BUNDLE_EOVERFLOW. */
+#define BUNDLE_FLAG_INK_STATS 4 /* record, per iteration, the ink of the drawing entering it
+                                   (occupied histogram cells): the convergence measure of
+                                   bundle_fetch_ink (Sec. 3.3, Fig. 3 compares convergence of
+                                   the two steps; fewer occupied cells = tighter bundles) */
 
 /* Result of bundle_get_info. */
 typedef struct {
@@ -216,6 +226,20 @@ bundle_ctx* bundle_batch_member(bundle_ctx* ctx, int32_t k);
  * for den <= 0 or a batch context. num is copied; applies from the next iteration.
  */
 bundle_status bundle_set_interaction(bundle_ctx* ctx, const int64_t* num, int64_t den);
+
+/*
+ * Convergence record (needs BUNDLE_FLAG_INK_STATS): for iterations first .. first+n-1
+ * (each < the context's iteration count and < BUNDLE_INK_STATS_CAP) writes
+ * out[2 i] = cells where any group's histogram is non-zero (the ink of the drawing
+ * entering iteration first+i, at grid resolution), out[2 i + 1] = the sum over groups of
+ * each group's non-zero cells (minus out[2 i]: cells shared by several groups, the
+ * overlaps between groups that Sec. 3.3 sees fall as bundling proceeds). With
+ * BUNDLE_FLAG_SEGMENT_HIST the histogram is the rasterised drawing itself (Sec. 4).
+ * out: host int64 [2 n]. Synchronises the stream. EINVAL for a range outside the record,
+ * ESTATE without the flag or for a batch context (ask its members).
+ */
+#define BUNDLE_INK_STATS_CAP 4096
+bundle_status bundle_fetch_ink(bundle_ctx* ctx, int64_t* out, int32_t first, int32_t n);
 
 /* Sizes, widths, map, schedule and point counts of a context (synchronises the stream).
  * For a batch: sums of the counts over its graphs; sizes and map of graph 0. */

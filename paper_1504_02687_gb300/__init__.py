@@ -25,6 +25,9 @@ BUNDLE_EOVERFLOW, BUNDLE_ETIMEOUT, BUNDLE_ESTATE, BUNDLE_ENOTSUP = 4, 5, 6, 7
 RHO_F32, RHO_BF16, RHO_F16 = 0, 1, 2
 INPUT_DEVICE = 1
 FLAG_FIXED_STEP = 1
+FLAG_SEGMENT_HIST = 2
+FLAG_INK_STATS = 4
+INK_STATS_CAP = 4096
 FETCH_DEVICE, FETCH_PIXELS, FETCH_RESAMPLED = 1, 2, 4
 DENSITY_HIST, DENSITY_SUMS, DENSITY_RHO = 0, 1, 2
 PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "combine",
@@ -35,7 +38,7 @@ EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bu
             "bundle_destroy", "bundle_last_error", "bundle_status_string",
             "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc",
             "bundle_init_batch", "bundle_batch_size", "bundle_batch_member",
-            "bundle_set_interaction")
+            "bundle_set_interaction", "bundle_fetch_ink")
 
 
 class BundleParams(ctypes.Structure):
@@ -131,6 +134,8 @@ def lib():
     L.bundle_batch_member.argtypes = [P, i32]
     L.bundle_batch_member.restype = P
     L.bundle_set_interaction.argtypes = [P, P, i64]
+    L.bundle_fetch_ink.argtypes = [P, P, i32, i32]
+    L.bundle_fetch_ink.restype = i32
     L.bundle_set_interaction.restype = i32
     _lib = L
     return L
@@ -261,6 +266,14 @@ def bundle_set_interaction(ctx, num, den: int):
     """General interaction matrix M = num / den (G x G integers, Eq. 3)."""
     n = np.ascontiguousarray(num, dtype=np.int64)
     _check(lib().bundle_set_interaction(ctx, _ptr(n), int(den)), ctx)
+
+
+def bundle_fetch_ink(ctx, first: int, n: int) -> np.ndarray:
+    """Convergence record (FLAG_INK_STATS): int64 [n, 2] of (cells any group occupies,
+    sum over groups of each group's occupied cells) for iterations first .. first+n-1."""
+    out = np.zeros((max(int(n), 0), 2), np.int64)
+    _check(lib().bundle_fetch_ink(ctx, _ptr(out), int(first), int(n)), ctx)
+    return out
 
 
 def bundle_iterate(ctx, n_iters: int):

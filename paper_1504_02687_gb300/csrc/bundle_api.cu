@@ -29,6 +29,10 @@ struct bundle_ctx {
     float den_f = 1.0f;
     double sum_bound = 0;        // worst-case smoothed sum (size_integers)
     int64_t* mix = nullptr;      // optional G x G interaction numerators (device)
+    unsigned long long mass_allowed = 0;  // segment histogram: largest mass the sums can take
+    int32_t* d_flag = nullptr;           // sticky overflow flag set on the device
+    unsigned long long* ink = nullptr;   // [BUNDLE_INK_STATS_CAP][2] convergence record
+    int n_sm = 0;
     double map[5] = {0, 0, 1, 0, 0};
     int32_t iteration = 0;
     int device = 0;
@@ -45,7 +49,7 @@ struct bundle_ctx {
     void* S = nullptr;
     void* rho = nullptr;
     void* quads = nullptr;
-    unsigned long long* counters = nullptr;  // [0] points splatted in total, [1] scratch sum
+    unsigned long long* counters = nullptr;  // [0] points splatted, [1] scratch sum, [2] segment mass
     int64_t* fetch_off = nullptr;
     int64_t* fetch_tmp = nullptr;
     float2* fetch_xy = nullptr;
@@ -139,7 +143,7 @@ void free_ctx(bundle_ctx* c) {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->perm, c->group, c->weight, c->cnt[0], c->cnt[1], c->pts[0], c->pts[1],
-                    c->hist, c->Y, c->S, c->rho, c->quads, c->mix, c->counters, c->fetch_off, c->fetch_tmp,
+                    c->hist, c->Y, c->S, c->rho, c->quads, c->mix, c->d_flag, c->ink, c->counters, c->fetch_off, c->fetch_tmp,
                     c->fetch_xy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -194,7 +198,8 @@ bundle_status check_params(const bundle_params& p, int32_t n_groups, std::string
     if (p.rho_dtype < 0 || p.rho_dtype > 2) return fail(e, BUNDLE_EINVAL, "bad rho_dtype");
     if (p.grid_dominant < 2 || p.grid_dominant > 4096)
         return fail(e, BUNDLE_EINVAL, "grid_dominant must be in [2, 4096]");
-    if ((p.flags & ~BUNDLE_FLAG_FIXED_STEP) != 0)
+    if ((p.flags & ~(BUNDLE_FLAG_FIXED_STEP | BUNDLE_FLAG_SEGMENT_HIST |
+                     BUNDLE_FLAG_INK_STATS)) != 0)
         return fail(e, BUNDLE_EINVAL, "unknown bits in flags");
     if (!(p.directed_offset >= 0 && p.directed_offset < 0.25f))
         return fail(e, BUNDLE_EINVAL, "directed_offset must be in [0, 0.25)");
@@ -225,7 +230,20 @@ bundle_status size_integers(bundle_ctx* c, const int32_t* weight_host, std::stri
     const double s = (double)(2 * c->p.radius + 1) * (double)(2 * c->p.radius + 1);
     double bound = 4.0 * M0;
     for (int p = 1; p < c->p.passes; ++p) bound *= s;
+    if (c->p.flags & BUNDLE_FLAG_SEGMENT_HIST) {
+        // a segment adds at most w_e to any cell, so cells stay below M0 as for points, but
+        // the mass (one count per rasterised cell) has no tight static bound: 64-bit sums,
+        // and the mass each iteration splats is checked on the device against what they hold
+        if (c->p.sum_bits == 32)
+            return fail(e, BUNDLE_EINVAL, "the segment histogram needs 64-bit sums");
+        double per_mass = 4.0;
+        for (int p = 1; p < c->p.passes; ++p) per_mass *= s;
+        const double mix = c->G > 1 ? (double)c->p.alpha_den * (c->G - 1) + c->p.alpha_num : 1.0;
+        c->mass_allowed = (unsigned long long)std::floor(two63 * (1 - 1e-12) / (per_mass * mix));
+        bound = 0;  // replaced by the run-time check
+    }
     int bits = c->p.sum_bits;
+    if (c->p.flags & BUNDLE_FLAG_SEGMENT_HIST) bits = 64;
     if (bits == 0) bits = bound < two31 * (1 - 1e-12) ? 32 : 64;
     if (bits == 32 && !(bound < two31 * (1 - 1e-12)))
         return fail(e, BUNDLE_EOVERFLOW, "smoothed-sum bound %.6g does not fit int32", bound);
@@ -360,6 +378,14 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
                        (size_t)c->G * quad_elems(c->W, c->H) * 4 * rho_bytes(c->p.rho_dtype)));
     CUDA_TRY(e, dalloc(c, &c->counters, 4));
     CUDA_TRY(e, dalloc(c, &c->d_iter, 1));
+    CUDA_TRY(e, dalloc(c, &c->d_flag, 1));
+    CUDA_TRY(e, cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream));
+    if (c->p.flags & BUNDLE_FLAG_INK_STATS) {
+        CUDA_TRY(e, dalloc(c, &c->ink, 2 * (size_t)BUNDLE_INK_STATS_CAP));
+        CUDA_TRY(e, cudaMemsetAsync(c->ink, 0, 2 * sizeof(unsigned long long) * BUNDLE_INK_STATS_CAP,
+                                    c->stream));
+        CUDA_TRY(e, cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    }
     CUDA_TRY(e, dalloc(c, &c->fetch_off, (size_t)E + 1));
     CUDA_TRY(e, dalloc(c, &c->fetch_tmp, scan_offsets_tmp_elems(E) + 1));
     CUDA_TRY(e, cudaMemsetAsync(c->hist, 0, C * kHistCopies * sizeof(uint32_t), c->stream));
@@ -512,6 +538,8 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
     a.n_max = c->p.n_max;
     a.delta = c->p.delta_px;
     a.fixed_step = (c->p.flags & BUNDLE_FLAG_FIXED_STEP) ? 1 : 0;
+    a.seg_hist = (c->p.flags & BUNDLE_FLAG_SEGMENT_HIST) ? 1 : 0;
+    a.mass = a.seg_hist ? c->counters + 2 : nullptr;
     // the directed offset applies to the first sampling of the run only
     a.dir_amount = (mode == kModeResample && c->iteration == 0)
                        ? (float)((double)c->p.directed_offset * std::max(c->W, c->H))
@@ -522,9 +550,13 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
                                             (size_t)kHistCopies * c->G * c->H * c->W * sizeof(uint32_t),
                                             c->stream);
                  }));
+    if (a.seg_hist && (mode & kModeResample))
+        CUDA_TRY(&c->err, cudaMemsetAsync(c->counters + 2, 0, sizeof(unsigned long long), c->stream));
     const int kind = mode == kModeResample ? kProfResample
                      : mode == kModeAdvect ? kProfAdvect : kProfAdvectResample;
     CUDA_TRY(&c->err, timed(c, kind, [&] { return launch_step(mode, c->p.rho_dtype, a, c->stream); }));
+    if (a.seg_hist && (mode & kModeResample))
+        CUDA_TRY(&c->err, launch_check_mass(c->counters + 2, c->mass_allowed, c->d_flag, c->stream));
     return BUNDLE_OK;
 }
 
@@ -545,6 +577,9 @@ bundle_status run_filter(bundle_ctx* c) {
     f.mix_self = c->mix_self;
     f.mix_all = c->mix_all;
     f.den_f = c->den_f;
+    if (c->ink)
+        CUDA_TRY(&c->err, launch_ink(c->hist, (int64_t)c->H * c->W, c->G, kHistCopies, c->ink,
+                                     c->d_iter, BUNDLE_INK_STATS_CAP, c->n_sm, c->stream));
     CUDA_TRY(&c->err, timed(c, kProfRowbox, [&] { return launch_rowbox(c->sum_bits, f, c->stream); }));
     CUDA_TRY(&c->err, timed(c, kProfColbox, [&] { return launch_colbox(c->sum_bits, f, c->stream); }));
     CUDA_TRY(&c->err, timed(c, kProfCombine, [&] {
@@ -1044,13 +1079,51 @@ bundle_ctx* bundle_batch_member(bundle_ctx* c, int32_t k) {
     return c->members[(size_t)k];
 }
 
+// Deferred device-side errors (segment histogram overflow). Synchronises the stream.
+static bundle_status check_device_flag(bundle_ctx* c) {
+    if (!c->d_flag) return BUNDLE_OK;
+    int32_t f = 0;
+    CUDA_TRY(&c->err, cudaMemcpyAsync(&f, c->d_flag, sizeof f, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    if (f)
+        return fail(&c->err, BUNDLE_EOVERFLOW,
+                    "segment histogram mass exceeded %llu: the int64 smoothed sums could wrap",
+                    c->mass_allowed);
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_fetch_ink(bundle_ctx* c, int64_t* out, int32_t first, int32_t n) {
+    if (!c) return BUNDLE_EINVAL;
+    if (!c->members.empty() || !c->ink)
+        return fail(&c->err, BUNDLE_ESTATE,
+                    "bundle_fetch_ink: the context was not created with BUNDLE_FLAG_INK_STATS "
+                    "(a batch records per member)");
+    if (!out || first < 0 || n < 0 || (int64_t)first + n > c->iteration ||
+        (int64_t)first + n > BUNDLE_INK_STATS_CAP)
+        return fail(&c->err, BUNDLE_EINVAL,
+                    "bundle_fetch_ink: iterations [%d, %d) outside the record [0, %d)", first,
+                    first + n, std::min<int32_t>(c->iteration, BUNDLE_INK_STATS_CAP));
+    if (n == 0) return BUNDLE_OK;
+    DeviceGuard dg(c->device);
+    if (bundle_status fs = check_device_flag(c)) return fs;
+    CUDA_TRY(&c->err, cudaMemcpyAsync(out, c->ink + 2 * (size_t)first,
+                                      2 * sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    return BUNDLE_OK;
+}
+
 bundle_status bundle_sync(bundle_ctx* c) {
     if (!c) return BUNDLE_EINVAL;
     DeviceGuard dg(c->device);
     for (bundle_ctx* m : c->members) CUDA_TRY(&c->err, cudaStreamSynchronize(m->stream));
     CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
     CUDA_TRY(&c->err, cudaGetLastError());
-    return BUNDLE_OK;
+    for (bundle_ctx* m : c->members) {
+        bundle_status s = check_device_flag(m);
+        if (s != BUNDLE_OK) return fail(&c->err, s, "%s", m->err.c_str());
+    }
+    return check_device_flag(c);
 }
 
 bundle_status bundle_fetch(bundle_ctx* c, int64_t* off, float* xy, int64_t cap,
@@ -1066,6 +1139,7 @@ bundle_status bundle_fetch(bundle_ctx* c, int64_t* off, float* xy, int64_t cap,
         sel = c->cur_R;
     }
     DeviceGuard dg(c->device);
+    if (bundle_status fs = check_device_flag(c)) return fs;
     const bool dev = (flags & BUNDLE_FETCH_DEVICE) != 0;
     const bool pix = (flags & BUNDLE_FETCH_PIXELS) != 0;
     CUDA_TRY(&c->err, launch_counts_to_caller(c->perm, c->cnt[sel], c->E, c->fetch_off, c->stream));
@@ -1135,6 +1209,7 @@ bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int6
         return fail(&c->err, BUNDLE_EINVAL, "dst holds %lld bytes, %zu needed",
                     (long long)dst_bytes, bytes);
     DeviceGuard dg(c->device);
+    if (bundle_status fs = check_device_flag(c)) return fs;
     if (which == BUNDLE_DENSITY_HIST)
         CUDA_TRY(&c->err, launch_fold_hist(c->hist, (int64_t)C, kHistCopies, c->stream));
     CUDA_TRY(&c->err, cudaMemcpyAsync(dst, src, bytes,

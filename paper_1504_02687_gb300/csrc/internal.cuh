@@ -56,6 +56,8 @@ struct StepArgs {
     float delta;
     int32_t fixed_step;      // KDEEB step: exactly h, no density test
     float dir_amount;        // directed graphs: normal offset (px) of interior resampled points
+    int32_t seg_hist;        // histogram by Bresenham segments instead of points
+    unsigned long long* mass;  // total weight splatted by this launch (segment mode)
 };
 
 struct FilterArgs {
@@ -93,6 +95,10 @@ cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cud
 cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st);
 // Fold histogram copies 1.. into copy 0 (their sum is unchanged), n cells per copy.
 cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t st);
+// Ink statistics of the histogram into stats[2 * (*iter)] (skipped past stats_cap).
+cudaError_t launch_ink(const uint32_t* hist, int64_t cells, int G, int copies,
+                       unsigned long long* stats, const int32_t* iter, int32_t stats_cap,
+                       int n_sm, cudaStream_t st);
 
 // Init / fetch helpers (point layout <-> caller order).
 cudaError_t launch_edge_keys(const float2* src, const float2* dst, const int32_t* group,
@@ -122,6 +128,9 @@ cudaError_t launch_sum_counts(const int32_t* cnt, int64_t E, unsigned long long*
                               cudaStream_t st);
 // Device iteration counter used with the device schedule of h (graph-friendly).
 cudaError_t launch_set_iter(int32_t* iter, int32_t value, cudaStream_t st);
+// Sticky overflow flag: set when *mass > allowed.
+cudaError_t launch_check_mass(const unsigned long long* mass, unsigned long long allowed,
+                              int32_t* flag, cudaStream_t st);
 cudaError_t launch_advance_iter(int32_t* iter, cudaStream_t st);
 size_t scan_offsets_tmp_elems(int64_t E);
 

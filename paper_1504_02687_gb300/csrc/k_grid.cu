@@ -415,6 +415,45 @@ __global__ void k_fold_hist(uint32_t* hist, int64_t n, int copies) {
     hist[i] = v;
 }
 
+// Ink of the drawing entering an iteration, from its histogram: cells where any group
+// counts something, and the sum over groups of each group's occupied cells (their
+// difference counts the cells that several groups share). Row it of `stats` gets both.
+__global__ void k_ink(const uint32_t* __restrict__ hist, int64_t cells, int G, int copies,
+                      unsigned long long* stats, const int32_t* iter, int32_t stats_cap) {
+    const int it = *iter;
+    if (it < 0 || it >= stats_cap) return;
+    unsigned long long any = 0, per_group = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += stride) {
+        int occ = 0;
+        for (int g = 0; g < G; ++g) {
+            uint32_t v = 0;
+            for (int k = 0; k < copies; ++k) v |= __ldg(hist + ((int64_t)k * G + g) * cells + i);
+            occ += v != 0;
+        }
+        any += occ != 0;
+        per_group += occ;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        any += __shfl_xor_sync(0xffffffffu, any, o);
+        per_group += __shfl_xor_sync(0xffffffffu, per_group, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (any | per_group)) {
+        atomicAdd(stats + 2 * (int64_t)it, any);
+        atomicAdd(stats + 2 * (int64_t)it + 1, per_group);
+    }
+}
+
+cudaError_t launch_ink(const uint32_t* hist, int64_t cells, int G, int copies,
+                       unsigned long long* stats, const int32_t* iter, int32_t stats_cap,
+                       int n_sm, cudaStream_t st) {
+    const int64_t want = (cells + 255) / 256;
+    const int blocks = (int)(want < 4 * n_sm ? want : 4 * n_sm);
+    k_ink<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(hist, cells, G, copies, stats, iter, stats_cap);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t st) {
     if (copies <= 1 || n <= 0) return cudaSuccess;
     k_fold_hist<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(hist, n, copies);

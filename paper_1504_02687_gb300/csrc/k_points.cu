@@ -169,12 +169,44 @@ __device__ __forceinline__ float warp_scan_incl(float x, int lane) {
 
 constexpr int kWarps = kStepThreads / 32;
 
+// Segment histogram (Eq. 1 as rasterised in Sec. 4): the cells from the cell of A to
+// the cell of B by the integer Bresenham line algorithm, each gaining w (the first
+// one skipped for segments after the first: it closed the previous segment).
+// Returns the number of cells counted.
+__device__ __forceinline__ int raster_segment(uint32_t* hl, int W, int H, float2 A, float2 B,
+                                              bool skip_first, unsigned w) {
+    int x = min(max((int)floorf(A.x), 0), W - 1), y = min(max((int)floorf(A.y), 0), H - 1);
+    const int x1 = min(max((int)floorf(B.x), 0), W - 1), y1 = min(max((int)floorf(B.y), 0), H - 1);
+    const int dx = abs(x1 - x), dy = -abs(y1 - y);
+    const int sx = x < x1 ? 1 : -1, sy = y < y1 ? 1 : -1;
+    int err = dx + dy, count = 0;
+    bool first = true;
+    for (;;) {
+        if (!(first && skip_first)) {
+            atomicAdd(hl + (size_t)y * W + x, w);
+            ++count;
+        }
+        first = false;
+        if (x == x1 && y == y1) break;
+        const int e2 = 2 * err;
+        if (e2 >= dy) {
+            err += dy;
+            x += sx;
+        }
+        if (e2 <= dx) {
+            err += dx;
+            y += sy;
+        }
+    }
+    return count;
+}
+
 // Write one resampled point and splat it: it adds its edge weight to its group's cell
 // (Eq. 1, Eq. 3) in one of the histogram copies.
 __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at, float2 R,
                                      int w) {
     a.pts_out[at] = R;
-    if (w != 0) {
+    if (w != 0 && !a.seg_hist) {
         const int cx = min(max((int)floorf(R.x), 0), a.W - 1);
         const int cy = min(max((int)floorf(R.y), 0), a.H - 1);
         atomicAdd(hl + (size_t)cy * a.W + cx, (unsigned)w);
@@ -355,6 +387,17 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                                             clamp_pos(__fadd_rn(R.y, oy), a.H));
                         emit(a, hl, ob + j, R, w);
                     }
+                }
+                if (a.seg_hist && w != 0) {
+                    // segments of the new polyline (its points were written by this warp)
+                    __syncwarp();
+                    unsigned long long cells = 0;
+                    for (int j = 1 + lane; j < m; j += 32)
+                        cells += raster_segment(hl, a.W, a.H, a.pts_out[ob + j - 1],
+                                                a.pts_out[ob + j], j >= 2, (unsigned)w);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(0xffffffffu, cells, o);
+                    if (lane == 0 && a.mass) atomicAdd(a.mass, cells * (unsigned long long)w);
                 }
                 if (lane == 0) a.cnt_out[e0 + i] = m;
             }
@@ -597,6 +640,10 @@ __global__ void k_sum_counts(const int32_t* __restrict__ cnt, int64_t E,
 }
 
 __global__ void k_set_iter(int32_t* iter, int32_t value) { *iter = value; }
+__global__ void k_check_mass(const unsigned long long* mass, unsigned long long allowed,
+                             int32_t* flag) {
+    if (*mass > allowed) *flag = 1;
+}
 __global__ void k_advance_iter(int32_t* iter) { *iter += 1; }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -681,6 +728,12 @@ cudaError_t launch_layout_to_caller(const int32_t* perm, const int32_t* cnt, con
 
 cudaError_t launch_set_iter(int32_t* iter, int32_t value, cudaStream_t st) {
     k_set_iter<<<1, 1, 0, st>>>(iter, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_mass(const unsigned long long* mass, unsigned long long allowed,
+                              int32_t* flag, cudaStream_t st) {
+    k_check_mass<<<1, 1, 0, st>>>(mass, allowed, flag);
     return cudaGetLastError();
 }
 

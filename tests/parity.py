@@ -30,7 +30,9 @@ def oracle_params(p) -> oracle.Params:
     return oracle.Params(radius=p.radius, passes=p.passes, alpha_num=p.alpha_num,
                          alpha_den=p.alpha_den, h_max_sigmas=p.h_max_sigmas, lam=p.lambda_,
                          n_fixed=p.n_fixed, n_max=p.n_max, delta=float(p.delta_px),
-                         beta=float(p.laplace_beta), eps=float(p.eps), tries=p.step_tries)
+                         beta=float(p.laplace_beta), eps=float(p.eps), tries=p.step_tries,
+                         fixed_step=bool(p.flags & pkg.FLAG_FIXED_STEP),
+                         segment_hist=bool(p.flags & pkg.FLAG_SEGMENT_HIST))
 
 
 def fetch_px(ctx, resampled=False):

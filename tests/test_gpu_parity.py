@@ -90,8 +90,12 @@ def _lockstep_once(ctx, w, p, max_bad_frac=1e-3, M=None):
     assert worst <= 8 * max(p.n_fixed, p.n_max) * 2.0 ** -23 * extent, worst
     # histogram of the GPU's resampled points (Eq. 1, Eq. 3): bit for bit
     group = w.group
-    np.testing.assert_array_equal(hist, oracle.splat(offR, R, group, w.weight, G, H, W))
-    assert hist.sum() == (np.diff(offR) * (w.weight if w.weight is not None else 1)).sum()
+    if p.flags & pkg.FLAG_SEGMENT_HIST:
+        np.testing.assert_array_equal(hist, oracle.splat_segments(offR, R, group, w.weight,
+                                                                  G, H, W))
+    else:
+        np.testing.assert_array_equal(hist, oracle.splat(offR, R, group, w.weight, G, H, W))
+        assert hist.sum() == (np.diff(offR) * (w.weight if w.weight is not None else 1)).sum()
     # box passes (Sec. 3.1): bit for bit
     np.testing.assert_array_equal(S, oracle.smooth(hist, p.radius, p.passes))
     # layer mix (Eq. 3, Eq. 4): exact integer numerator, one FP32 rounding and division
@@ -293,6 +297,85 @@ def test_variants_fixed_step_directed_offset():
             _lockstep_once(ctx, w, p)
         finally:
             pkg.bundle_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["g1-fixed32", "g3-bylength-weighted"])
+def test_segment_histogram_lockstep(name):
+    """Histogram by Bresenham segments (Eq. 1 as rasterised in Sec. 4): every stage of two
+    iterations from straight edges and one from bundled polylines against the oracle."""
+    w, p, ctx = _make(name, flags=pkg.FLAG_SEGMENT_HIST)
+    try:
+        _lockstep_once(ctx, w, p)
+        _lockstep_once(ctx, w, p)
+        pkg.bundle_iterate(ctx, 2)
+        _lockstep_once(ctx, w, p)
+        pkg.bundle_sync(ctx)
+    finally:
+        pkg.bundle_destroy(ctx)
+
+
+def test_segment_histogram_mass_overflow_is_reported():
+    """With r = 3 and k = 16 the int64 sums hold no segment mass at all: the device check
+    flags the first iteration and the next sync reports it (sums wrap modulo 2^64 on the
+    device, nothing faults)."""
+    w, p, ctx = _make("g1-fixed32", flags=pkg.FLAG_SEGMENT_HIST, radius=3, passes=16)
+    try:
+        pkg.bundle_iterate(ctx, 1)
+        with pytest.raises(pkg.BundleError, match="segment histogram") as ei:
+            pkg.bundle_sync(ctx)
+        assert ei.value.status == pkg.BUNDLE_EOVERFLOW
+    finally:
+        pkg.bundle_destroy(ctx)
+
+
+def test_ink_record_matches_histograms():
+    """The convergence record (occupied cells per iteration) equals the counts of the fetched
+    histogram at every iteration, and the captured-graph path records the same numbers."""
+    for flags in (pkg.FLAG_INK_STATS, pkg.FLAG_INK_STATS | pkg.FLAG_SEGMENT_HIST):
+        w, p, ctx = _make("g3-bylength-weighted", flags=flags)
+        w2, p2, ctx2 = _make("g3-bylength-weighted", flags=flags)
+        try:
+            expect = []
+            for _ in range(4):
+                pkg.bundle_iterate(ctx, 1)
+                expect.append(oracle.ink(pkg.bundle_fetch_density(ctx, pkg.DENSITY_HIST)))
+            np.testing.assert_array_equal(pkg.bundle_fetch_ink(ctx, 0, 4), np.array(expect))
+            pkg.bundle_iterate(ctx2, 4)          # one call: steady iterations through graphs
+            np.testing.assert_array_equal(pkg.bundle_fetch_ink(ctx2, 0, 4), np.array(expect))
+            with pytest.raises(pkg.BundleError) as ei:
+                pkg.bundle_fetch_ink(ctx2, 2, 3)
+            assert ei.value.status == pkg.BUNDLE_EINVAL
+        finally:
+            pkg.bundle_destroy(ctx)
+            pkg.bundle_destroy(ctx2)
+    w, p, ctx = _make("g1-fixed32")
+    try:
+        pkg.bundle_iterate(ctx, 1)
+        with pytest.raises(pkg.BundleError) as ei:
+            pkg.bundle_fetch_ink(ctx, 0, 1)
+        assert ei.value.status == pkg.BUNDLE_ESTATE
+    finally:
+        pkg.bundle_destroy(ctx)
+
+
+def test_optimised_step_converges_in_fewer_iterations():
+    """Sec. 3.3 / Fig. 3 on the CUDA path: the ink of the segment-rasterised drawing falls
+    faster with the density test than with KDEEB's fixed step (1,000-edge uniform graph)."""
+    w = synth.small(n_edges=1000)
+    ink = {}
+    for fixed in (0, pkg.FLAG_FIXED_STEP):
+        p = params_for(w, flags=fixed | pkg.FLAG_SEGMENT_HIST | pkg.FLAG_INK_STATS)
+        ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+        try:
+            pkg.bundle_iterate(ctx, 10)
+            ink[fixed] = pkg.bundle_fetch_ink(ctx, 0, 10)[:, 0]
+        finally:
+            pkg.bundle_destroy(ctx)
+    opt, fix = ink[0], ink[pkg.FLAG_FIXED_STEP]
+    print("ink optimised", opt.tolist(), "fixed", fix.tolist())
+    assert opt[0] == fix[0]
+    assert (opt[1:] < fix[1:]).all()
+    assert np.flatnonzero(opt <= fix[-1])[0] <= 8
 
 
 def test_optimised_step_never_lowers_density():
