@@ -389,10 +389,8 @@ def run_ours(args):
     }
 
     if not args.no_variants and world == 1 and args.rho == "f32":
-        var = {}
-        for rho in ("bf16",):
-            p2 = params_of(w, rho)
-            c2 = pkg.bundle_init(p2, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight,
+        def timed_variant(wl, prm, steps):
+            c2 = pkg.bundle_init(prm, wl.src_xy, wl.dst_xy, wl.group, wl.n_groups, wl.weight,
                                  stream=stream)
             pkg.bundle_iterate(c2, max(args.warmup, 3))
             pkg.bundle_sync(c2)
@@ -401,13 +399,44 @@ def run_ours(args):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            pkg.bundle_iterate(c2, args.steps)
+            pkg.bundle_iterate(c2, steps)
             b.record(stream)
             torch.cuda.synchronize()
             m2 = a.elapsed_time(b)
             u2 = pkg.bundle_get_info(c2).points_processed - d0
-            var[rho] = {"value": u2 / (m2 / 1e3), "ms_per_step": m2 / args.steps}
             pkg.bundle_destroy(c2)
+            return {"value": u2 / (m2 / 1e3), "ms_per_step": m2 / steps}
+
+        var = {"bf16": timed_variant(w, params_of(w, "bf16"), args.steps)}
+        # KDEEB's fixed step (Sec. 3.3) on the same workload: the cost of the density test
+        pf = params_of(w, args.rho)
+        pf.flags = pkg.FLAG_FIXED_STEP
+        var["fixed_step"] = timed_variant(w, pf, args.steps)
+        # Bresenham segment histogram (Eq. 1 as rasterised in Sec. 4) against the point splat
+        # on the 1M-edge spatial-only workload (its int64 sums hold the segment mass; the
+        # 8-group stack with r = 12, k = 4 does not)
+        wc = make_workload("clustered", 0)
+        pc = params_of(wc, args.rho)
+        ps = params_of(wc, args.rho)
+        ps.flags = pkg.FLAG_SEGMENT_HIST
+        var["segment_hist"] = {"workload": wc.name, **timed_variant(wc, ps, args.steps),
+                               "point_splat": timed_variant(wc, pc, args.steps)}
+        # Fig. 3: ink of the segment-rasterised drawing entering each of 10 iterations,
+        # optimised vs fixed step, on the 1,000-edge uniform graph
+        from paper_1504_02687_gb300 import synth
+
+        wsm = synth.small(n_edges=1000)
+        conv = {"workload": "uniform-1000-edges-256sq", "measure": "occupied cells entering "
+                "each iteration (segment histogram)"}
+        for name, fl in (("optimised", 0), ("fixed", pkg.FLAG_FIXED_STEP)):
+            pm = params_of(wsm, args.rho)
+            pm.flags = fl | pkg.FLAG_SEGMENT_HIST | pkg.FLAG_INK_STATS
+            c4 = pkg.bundle_init(pm, wsm.src_xy, wsm.dst_xy, wsm.group, wsm.n_groups, wsm.weight,
+                                 stream=stream)
+            pkg.bundle_iterate(c4, 10)
+            conv[name] = pkg.bundle_fetch_ink(c4, 0, 10)[:, 0].tolist()
+            pkg.bundle_destroy(c4)
+        var["convergence"] = conv
         out["variants"] = var
 
     if not args.no_e2e:

@@ -79,6 +79,9 @@ def _load():
     lib.oracle_run_mode.argtypes = ([i64, P, P, P, P, i32, i32, i32, i32, i32, i32, i32, f64, f64,
                                      i32, i32, f64, f64, f64, i32, i32, i32, i32, f64, P, i32, P,
                                      P, i64, P, P, P, P, P, i64])
+    lib.oracle_render.argtypes = [i64, P, P, P, P, i32, i32, i32, P, i32, f64, f64, f64, f64,
+                                  i32, P, P, P, P, P]
+    lib.oracle_render.restype = i32
     lib.oracle_splat_segments.argtypes = [i64, P, P, P, P, i32, i32, i32, P]
     lib.oracle_splat_segments.restype = None
     lib.oracle_run_mode.restype = i64
@@ -178,6 +181,30 @@ def splat_segments(off, xy, group, weight, G, H, W):
     lib.oracle_splat_segments(off.shape[0] - 1, _p(off), _p(xy), _p(_c(group, np.int32)),
                               _p(_c(weight, np.int32)), G, H, W, _p(hist))
     return hist
+
+
+def render(off, xy, group, weight, rho, palette, scale=1, alpha=0.25, width_min=1.0,
+           width_max=4.0, rho_ref=0.0, log_width=False, background=(0, 0, 0)):
+    """Headless drawing of the polylines (Sec. 3.4): returns (accum int64 [Hi, Wi, 4],
+    ambiguous-pixel mask bool [Hi, Wi], rgba uint8 [Hi, Wi, 4])."""
+    lib = _load()
+    off = _c(off, np.int64)
+    xy = _c(xy, np.float64).reshape(-1, 2)
+    rho = _c(rho, np.float64)
+    G, H, W = rho.shape
+    Hi, Wi = H * scale, W * scale
+    pal = _c(palette, np.uint8).reshape(G, 3)
+    bg = np.ascontiguousarray(background, np.uint8)
+    acc = np.zeros((Hi, Wi, 4), np.int64)
+    amb = np.zeros((Hi, Wi), np.uint8)
+    rgba = np.zeros((Hi, Wi, 4), np.uint8)
+    rc = lib.oracle_render(off.shape[0] - 1, _p(off), _p(xy), _p(_c(group, np.int32)),
+                           _p(_c(weight, np.int32)), G, H, W, _p(rho), scale, alpha, width_min,
+                           width_max, rho_ref, 1 if log_width else 0, _p(pal), _p(bg), _p(acc),
+                           _p(amb), _p(rgba))
+    if rc != 0:
+        raise ValueError("oracle_render: invalid arguments")
+    return acc, amb.astype(bool), rgba
 
 
 def ink(hist):

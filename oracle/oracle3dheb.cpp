@@ -627,4 +627,96 @@ int64_t oracle_run_mode(int64_t n_edges, const int64_t* off_in, const double* xy
     return n;
 }
 
+/*
+ * Headless rendering of the bundled drawing (Sec. 3.4): polylines drawn as
+ * line segments coloured by bin, edge weight shown by alpha accumulation and by
+ * a line width that follows the density at the sample points. The paper draws
+ * with OpenGL; this restates what the drawing shows, as a definition:
+ *  - image = (W * scale) x (H * scale) pixels; pixel (px, py) has its centre at
+ *    (px + 0.5, py + 0.5) in image units, i.e. grid position / scale;
+ *  - segment j of edge e (points x_j, x_{j+1}, scaled to image units) has width
+ *    w = width_min + (width_max - width_min) u, u = clamp(rho_bar / rho_ref, 0, 1)
+ *    (log2(1 + u) with log_width), rho_bar the mean of the bilinear density of
+ *    the edge's own layer at x_j and x_{j+1}; rho_ref <= 0 means the maximum of
+ *    rho over the stack;
+ *  - the segment covers the pixels whose centre lies within w / 2 of it; a pixel
+ *    whose nearest point on segment j is its far end (t >= 1) belongs to segment
+ *    j + 1 instead (joints are drawn once), except on the last segment;
+ *  - alpha accumulation, order-free: every covered pixel gains the optical depth
+ *    tau_e = w_e * llround(-ln(1 - alpha) * 2^20) and tau_e times the bin's RGB;
+ *    the pixel's opacity is A = 1 - exp(-sum tau / 2^20) (what repeated "over"
+ *    with alpha gives) and its colour the tau-weighted mean of the edges' colours;
+ *  - final RGB = A * colour + (1 - A) * background, rounded half up to 8 bits,
+ *    alpha 255.
+ * accum: int64 [Hi][Wi][4] (sum tau, sum tau R, sum tau G, sum tau B); amb: 1
+ * where some coverage decision is within 1e-4 of its threshold (a float of lower
+ * precision may decide it either way); rgba: uint8 [Hi][Wi][4].
+ * Returns 0, or -1 for invalid arguments.
+ */
+int32_t oracle_render(int64_t n_edges, const int64_t* off, const double* xy, const int32_t* group,
+                      const int32_t* weight, int32_t G, int32_t H, int32_t W, const double* rho,
+                      int32_t scale, double alpha, double width_min, double width_max,
+                      double rho_ref, int32_t log_width, const uint8_t* palette,
+                      const uint8_t* background, int64_t* accum, uint8_t* amb, uint8_t* rgba) {
+    if (scale < 1 || !(alpha > 0 && alpha < 1) || !(width_min > 0) || width_max < width_min)
+        return -1;
+    const int64_t Wi = (int64_t)W * scale, Hi = (int64_t)H * scale;
+    const int64_t tau1 = std::llround(-std::log1p(-alpha) * 1048576.0);
+    if (rho_ref <= 0) {
+        rho_ref = 0;
+        for (int64_t i = 0; i < (int64_t)G * H * W; ++i) rho_ref = std::max(rho_ref, rho[i]);
+    }
+    std::fill(accum, accum + Hi * Wi * 4, (int64_t)0);
+    std::fill(amb, amb + Hi * Wi, (uint8_t)0);
+    for (int64_t e = 0; e < n_edges; ++e) {
+        const int g = group ? group[e] : 0;
+        const int64_t tau = (weight ? weight[e] : 1) * tau1;
+        const double* layer = rho + (int64_t)g * H * W;
+        const int64_t n = off[e + 1] - off[e];
+        const double* P = xy + 2 * off[e];
+        for (int64_t j = 0; j + 1 < n; ++j) {
+            const bool last = j + 2 == n;
+            double rb = (bilinear_density(layer, H, W, P[2 * j], P[2 * j + 1]) +
+                         bilinear_density(layer, H, W, P[2 * j + 2], P[2 * j + 3])) / 2;
+            double u = rho_ref > 0 ? std::min(std::max(rb / rho_ref, 0.0), 1.0) : 0.0;
+            if (log_width) u = std::log2(1 + u);
+            const double r = (width_min + (width_max - width_min) * u) / 2;
+            const double ax = P[2 * j] * scale, ay = P[2 * j + 1] * scale;
+            const double bx = P[2 * j + 2] * scale, by = P[2 * j + 3] * scale;
+            const double dx = bx - ax, dy = by - ay, L2 = dx * dx + dy * dy;
+            const int64_t x0 = std::max<int64_t>(0, (int64_t)std::floor(std::min(ax, bx) - r) - 1);
+            const int64_t x1 = std::min<int64_t>(Wi - 1, (int64_t)std::ceil(std::max(ax, bx) + r) + 1);
+            const int64_t y0 = std::max<int64_t>(0, (int64_t)std::floor(std::min(ay, by) - r) - 1);
+            const int64_t y1 = std::min<int64_t>(Hi - 1, (int64_t)std::ceil(std::max(ay, by) + r) + 1);
+            for (int64_t py = y0; py <= y1; ++py)
+                for (int64_t px = x0; px <= x1; ++px) {
+                    const double cx = px + 0.5, cy = py + 0.5;
+                    const double t = L2 > 0 ? ((cx - ax) * dx + (cy - ay) * dy) / L2 : 0.0;
+                    const double tc = std::min(std::max(t, 0.0), 1.0);
+                    const double qx = ax + tc * dx - cx, qy = ay + tc * dy - cy;
+                    const double d2 = qx * qx + qy * qy;
+                    const bool near_r = std::fabs(d2 - r * r) <= 1e-4 * std::max(r * r, 1.0);
+                    const bool near_t = !last && std::fabs(t - 1) <= 1e-4;
+                    if ((near_r || near_t) && d2 <= r * r * (1 + 1e-3) + 1e-4)
+                        amb[py * Wi + px] = 1;
+                    if (d2 > r * r || (!last && t >= 1)) continue;
+                    int64_t* a = accum + 4 * (py * Wi + px);
+                    a[0] += tau;
+                    for (int c = 0; c < 3; ++c) a[1 + c] += tau * palette[3 * g + c];
+                }
+        }
+    }
+    for (int64_t i = 0; i < Hi * Wi; ++i) {
+        const int64_t* a = accum + 4 * i;
+        const double A = 1 - std::exp(-(double)a[0] / 1048576.0);
+        for (int c = 0; c < 3; ++c) {
+            const double col = a[0] > 0 ? (double)a[1 + c] / (double)a[0] : 0.0;
+            const double v = A * col + (1 - A) * background[c];
+            rgba[4 * i + c] = (uint8_t)std::min(255.0, std::max(0.0, std::floor(v + 0.5)));
+        }
+        rgba[4 * i + 3] = 255;
+    }
+    return 0;
+}
+
 }  // extern "C"

@@ -498,3 +498,68 @@ def test_optimised_step_converges_in_fewer_iterations(oracle_mod):
     assert (ink[False][1:] < ink[True][1:]).all()
     assert np.flatnonzero(ink[False] <= ink[True][-1])[0] <= 8
     assert (np.diff(ink[False]) < 0).all()        # and the ink falls every iteration
+
+
+# ----------------------------------------------------------- headless rendering (Sec. 3.4)
+TAU_04 = 535639  # llround(-ln(1 - 0.4) * 2^20)
+
+
+def _render(oracle_mod, pts, G=1, group=None, weight=None, rho=None, H=8, W=10, **kw):
+    off = np.cumsum([0] + [len(p) for p in pts]).astype(np.int64)
+    xy = np.concatenate([np.asarray(p, float) for p in pts])
+    rho = np.zeros((G, H, W)) if rho is None else rho
+    pal = np.array([[255, 0, 0], [0, 0, 255], [0, 255, 0]][:G], np.uint8)
+    kw.setdefault("alpha", 0.4)
+    kw.setdefault("width_min", 1.0)
+    kw.setdefault("width_max", 1.0)
+    return oracle_mod.render(off, xy, group, weight, rho, pal, **kw)
+
+
+def _covered(acc):
+    return sorted(zip(*np.nonzero(acc[..., 0])))
+
+
+def test_render_single_segment(oracle_mod):
+    acc, amb, rgba = _render(oracle_mod, [[(2.5, 3.5), (7.5, 3.5)]])
+    assert _covered(acc) == [(3, x) for x in range(2, 8)]
+    assert (acc[3, 2:8, 0] == TAU_04).all() and (acc[3, 2:8, 1] == 255 * TAU_04).all()
+    assert not amb.any()
+    # opacity 1 - exp(-tau) = 0.4 over black: red 0.4 * 255 = 102
+    assert (rgba[3, 2:8] == [102, 0, 0, 255]).all()
+    assert (rgba[0, 0] == [0, 0, 0, 255]).all()
+
+
+def test_render_crossing_joint_and_weight(oracle_mod):
+    # red horizontal and blue vertical edge cross at pixel (3, 5): twice the depth, mixed colour
+    acc, amb, rgba = _render(oracle_mod, [[(2.5, 3.5), (7.5, 3.5)], [(5.5, 0.5), (5.5, 7.5)]],
+                             G=2, group=np.array([0, 1], np.int32))
+    assert acc[3, 5, 0] == 2 * TAU_04 and acc[3, 5, 1] == acc[3, 5, 3] == 255 * TAU_04
+    # A = 1 - 0.6^2 = 0.64 of the mean colour (127.5, 0, 127.5): 81.6 -> 82
+    assert (rgba[3, 5] == [82, 0, 82, 255]).all()
+    # an L-shaped polyline: the corner pixel is the end of one segment and the start of the
+    # next, and is drawn once
+    acc, amb, _ = _render(oracle_mod, [[(2.5, 2.5), (6.5, 2.5), (6.5, 6.5)]])
+    expect = {(2, x) for x in range(2, 7)} | {(y, 6) for y in range(2, 7)}
+    assert set(_covered(acc)) == expect and (acc[acc[..., 0] > 0, 0] == TAU_04).all()
+    # weight 2 draws like two unit edges on top of each other
+    a2, _, r2 = _render(oracle_mod, [[(2.5, 3.5), (7.5, 3.5)]], weight=np.array([2], np.int32))
+    a11, _, r11 = _render(oracle_mod, [[(2.5, 3.5), (7.5, 3.5)]] * 2)
+    np.testing.assert_array_equal(a2, a11)
+    np.testing.assert_array_equal(r2, r11)
+
+
+def test_render_width_from_density_and_scale(oracle_mod):
+    seg = [[(2.5, 3.5), (7.5, 3.5)]]
+    rho = np.ones((1, 8, 10))
+    # uniform density at the reference: full width 3 (radius 1.5): rows 2..4, columns 1..8
+    acc, amb, _ = _render(oracle_mod, seg, rho=rho, width_max=3.0)
+    assert _covered(acc) == [(y, x) for y in range(2, 5) for x in range(1, 9)]
+    assert not amb.any()
+    # u = 0.6 of the reference: width 1 + 2 * 0.6 = 2.2 (radius 1.1): the caps lose corners
+    acc, amb, _ = _render(oracle_mod, seg, rho=rho, width_max=3.0, rho_ref=1 / 0.6)
+    assert set(_covered(acc)) == ({(3, x) for x in range(1, 9)} | {(2, x) for x in range(2, 8)}
+                                  | {(4, x) for x in range(2, 8)})
+    # scale 2: the segment spans image x 5..15 on row 7.0; width 1.5 covers rows 6 and 7
+    acc, amb, _ = _render(oracle_mod, seg, scale=2, width_max=1.5, width_min=1.5)
+    assert acc.shape == (16, 20, 4)
+    assert _covered(acc) == [(y, x) for y in (6, 7) for x in range(4, 16)]
