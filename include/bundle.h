@@ -241,6 +241,49 @@ bundle_status bundle_set_interaction(bundle_ctx* ctx, const int64_t* num, int64_
 #define BUNDLE_INK_STATS_CAP 4096
 bundle_status bundle_fetch_ink(bundle_ctx* ctx, int64_t* out, int32_t first, int32_t n);
 
+/*
+ * Headless rendering of the current drawing (Sec. 3.4): polylines drawn as line
+ * segments coloured by bin, bundle weight shown by alpha accumulation and by a line
+ * width that follows the density at the sample points. OpenGL is not used; the
+ * image is a device computation:
+ *  - image: (grid_w * scale) x (grid_h * scale) pixels, pixel (px, py) centred at
+ *    (px + 0.5, py + 0.5) / scale in grid units;
+ *  - segment j of an edge has width w = width_min + (width_max - width_min) u, with
+ *    u = clamp(rho_bar / rho_ref, 0, 1) (log2(1 + u) when log_width), rho_bar the
+ *    mean of the bilinear density of the edge's own layer (the last iteration's map)
+ *    at its two points; rho_ref <= 0: the largest density of the stack;
+ *  - it covers the pixels whose centre is within w / 2 of it; a pixel nearest to a
+ *    segment's far end (projection t >= 1) is left to the next segment, so joints
+ *    are drawn once (the last segment keeps its end);
+ *  - each covered pixel gains the optical depth tau_e = w_e * llround(-ln(1 - alpha)
+ *    * 2^20) and tau_e times the bin's RGB (integer sums: independent of order); the
+ *    pixel's opacity is 1 - exp(-sum tau / 2^20), its colour the tau-weighted mean,
+ *    composited over the background and rounded to 8 bits, alpha 255.
+ */
+typedef struct {
+    int32_t scale;         /* 1..16 */
+    float alpha;           /* opacity of one unit-weight edge, 0 < alpha < 1 */
+    float width_min;       /* image pixels, 1 <= width_min <= width_max <= 64 */
+    float width_max;
+    float rho_ref;         /* density drawn at width_max; <= 0: the stack's maximum */
+    int32_t log_width;     /* 0: linear in u; 1: log2(1 + u) */
+    uint8_t background[4]; /* RGB, the fourth byte unused */
+} bundle_render_params;
+
+/*
+ * palette: host uint8 [n_groups][3] RGB per bin (nominal bins: distinct colours;
+ * ordinal: a sequential table; Sec. 3.4). rgba: uint8 [Hi][Wi][4], host, or device
+ * with BUNDLE_FETCH_DEVICE. accum: optional int64 [Hi][Wi][4] (sum tau, sum tau R,
+ * sum tau G, sum tau B), same memory kind as rgba. Needs one finished iteration
+ * (ESTATE otherwise, and for a batch context: render its members). Allocates
+ * n_groups * Hi * Wi * 8 bytes of device workspace for the call (one depth map per
+ * bin; at most 2^30 cells, and Hi * Wi <= 2^28: EINVAL beyond); synchronises the
+ * stream.
+ */
+bundle_status bundle_render(bundle_ctx* ctx, const bundle_render_params* params,
+                            const uint8_t* palette, uint8_t* rgba, int64_t* accum,
+                            int32_t flags);
+
 /* Sizes, widths, map, schedule and point counts of a context (synchronises the stream).
  * For a batch: sums of the counts over its graphs; sizes and map of graph 0. */
 bundle_status bundle_get_info(const bundle_ctx* ctx, bundle_info* out);

@@ -38,7 +38,7 @@ EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bu
             "bundle_destroy", "bundle_last_error", "bundle_status_string",
             "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc",
             "bundle_init_batch", "bundle_batch_size", "bundle_batch_member",
-            "bundle_set_interaction", "bundle_fetch_ink")
+            "bundle_set_interaction", "bundle_fetch_ink", "bundle_render")
 
 
 class BundleParams(ctypes.Structure):
@@ -74,6 +74,15 @@ class BundleGraphDesc(ctypes.Structure):
     _fields_ = [
         ("n_edges", ctypes.c_int64), ("src_xy", ctypes.c_void_p), ("dst_xy", ctypes.c_void_p),
         ("group", ctypes.c_void_p), ("n_groups", ctypes.c_int32), ("weight", ctypes.c_void_p),
+    ]
+
+
+class BundleRenderParams(ctypes.Structure):
+    """Mirror of ``bundle_render_params``."""
+    _fields_ = [
+        ("scale", ctypes.c_int32), ("alpha", ctypes.c_float), ("width_min", ctypes.c_float),
+        ("width_max", ctypes.c_float), ("rho_ref", ctypes.c_float), ("log_width", ctypes.c_int32),
+        ("background", ctypes.c_uint8 * 4),
     ]
 
 
@@ -134,6 +143,8 @@ def lib():
     L.bundle_batch_member.argtypes = [P, i32]
     L.bundle_batch_member.restype = P
     L.bundle_set_interaction.argtypes = [P, P, i64]
+    L.bundle_render.argtypes = [P, ctypes.POINTER(BundleRenderParams), P, P, P, i32]
+    L.bundle_render.restype = i32
     L.bundle_fetch_ink.argtypes = [P, P, i32, i32]
     L.bundle_fetch_ink.restype = i32
     L.bundle_set_interaction.restype = i32
@@ -322,6 +333,44 @@ def bundle_fetch_density(ctx, which: int, out=None):
     flags = FETCH_DEVICE if _is_device(out) else 0
     _check(lib().bundle_fetch_density(ctx, int(which), _ptr(out), int(nbytes), flags), ctx)
     return out
+
+
+def hue_palette(n_groups: int) -> np.ndarray:
+    """Evenly spaced hues at full saturation and value: distinct colours for nominal bins
+    (Sec. 3.4). uint8 [n_groups, 3]."""
+    out = np.zeros((n_groups, 3), np.uint8)
+    for g in range(n_groups):
+        h = 6.0 * g / max(n_groups, 1)
+        k = int(h) % 6
+        f = h - int(h)
+        rgb = [(1, f, 0), (1 - f, 1, 0), (0, 1, f), (0, 1 - f, 1), (f, 0, 1), (1, 0, 1 - f)][k]
+        out[g] = [round(255 * c) for c in rgb]
+    return out
+
+
+def bundle_render(ctx, palette=None, scale: int = 1, alpha: float = 0.25,
+                  width_min: float = 1.0, width_max: float = 4.0, rho_ref: float = 0.0,
+                  log_width: bool = False, background=(0, 0, 0), rgba=None, accum=None):
+    """Draw the current polylines (Sec. 3.4). Returns rgba uint8 [Hi, Wi, 4] (numpy, or the
+    given device tensor); `accum` (int64 [Hi, Wi, 4], same memory kind) receives the raw
+    integer accumulators when given."""
+    info = bundle_get_info(ctx)
+    Hi, Wi = info.grid_h * scale, info.grid_w * scale
+    pal = hue_palette(info.n_groups) if palette is None else np.ascontiguousarray(palette, np.uint8)
+    if pal.shape != (info.n_groups, 3):
+        raise ValueError(f"palette must be uint8 [{info.n_groups}, 3]")
+    if rgba is None:
+        rgba = np.zeros((Hi, Wi, 4), np.uint8)
+    rp = BundleRenderParams(int(scale), float(alpha), float(width_min), float(width_max),
+                            float(rho_ref), 1 if log_width else 0)
+    for i, v in enumerate(background[:3]):
+        rp.background[i] = int(v)
+    flags = FETCH_DEVICE if _is_device(rgba) else 0
+    if accum is not None and _is_device(accum) != bool(flags):
+        raise ValueError("rgba and accum must both be host or both device buffers")
+    _check(lib().bundle_render(ctx, ctypes.byref(rp), _ptr(pal), _ptr(rgba), _ptr(accum), flags),
+           ctx)
+    return rgba
 
 
 def bundle_profile_enable(ctx, on: bool = True):

@@ -1113,6 +1113,114 @@ bundle_status bundle_fetch_ink(bundle_ctx* c, int64_t* out, int32_t first, int32
     return BUNDLE_OK;
 }
 
+bundle_status bundle_render(bundle_ctx* c, const bundle_render_params* rp,
+                            const uint8_t* palette, uint8_t* rgba, int64_t* accum,
+                            int32_t flags) {
+    if (!c) return BUNDLE_EINVAL;
+    if (!c->members.empty())
+        return fail(&c->err, BUNDLE_ESTATE, "render a batch's graphs through bundle_batch_member");
+    if (!rp || !palette || !rgba)
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_render: params, palette and rgba are required");
+    if (rp->scale < 1 || rp->scale > 16 || !(rp->alpha > 0.0f && rp->alpha < 1.0f) ||
+        !(rp->width_min >= 1.0f) || !(rp->width_max >= rp->width_min) ||
+        !(rp->width_max <= 64.0f) || !std::isfinite(rp->rho_ref) ||
+        (rp->log_width != 0 && rp->log_width != 1))
+        return fail(&c->err, BUNDLE_EINVAL,
+                    "bundle_render: need 1 <= scale <= 16, 0 < alpha < 1, "
+                    "1 <= width_min <= width_max <= 64, finite rho_ref, log_width 0 or 1");
+    const int64_t Wi = (int64_t)c->W * rp->scale, Hi = (int64_t)c->H * rp->scale;
+    if (Wi * Hi > ((int64_t)1 << 28) || (int64_t)c->G * Wi * Hi > ((int64_t)1 << 30))
+        return fail(&c->err, BUNDLE_EINVAL,
+                    "bundle_render: image of %lld x %lld pixels x %d bins is too large "
+                    "(at most 2^28 pixels and 2^30 depth cells)",
+                    (long long)Wi, (long long)Hi, c->G);
+    if (!c->have_density)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_render: run an iteration first (no density)");
+    DeviceGuard dg(c->device);
+    if (bundle_status fs = check_device_flag(c)) return fs;
+    const bool dev = (flags & BUNDLE_FETCH_DEVICE) != 0;
+    const int64_t npx = Wi * Hi;
+    unsigned long long* depth = nullptr;
+    int32_t* d_pal = nullptr;
+    unsigned int* d_ref = nullptr;
+    void* d_rgba = nullptr;
+    void* d_acc = nullptr;
+    auto cleanup = [&] {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(depth);
+        cudaFree(d_pal);
+        cudaFree(d_ref);
+        if (!dev) {
+            cudaFree(d_rgba);
+            cudaFree(d_acc);
+        }
+    };
+    std::vector<int32_t> pal((size_t)c->G * 3);
+    for (size_t i = 0; i < pal.size(); ++i) pal[i] = palette[i];
+    const float ref = rp->rho_ref > 0.0f ? rp->rho_ref : 0.0f;
+    unsigned int ref_bits;
+    std::memcpy(&ref_bits, &ref, sizeof ref_bits);
+    cudaError_t e = cudaMalloc(&depth, (size_t)c->G * npx * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_pal, pal.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_ref, sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        if (dev) {
+            d_rgba = rgba;
+            d_acc = accum;
+        } else {
+            e = cudaMalloc(&d_rgba, (size_t)npx * 4);
+            if (e == cudaSuccess && accum) e = cudaMalloc(&d_acc, (size_t)npx * 32);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(depth, 0, (size_t)c->G * npx * 8, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_pal, pal.data(), pal.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_ref, &ref_bits, sizeof ref_bits, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        RenderArgs a{};
+        a.cnt = c->cnt[c->cur_P];
+        a.pts = c->pts[c->cur_P];
+        a.group = c->group;
+        a.weight = c->weight;
+        a.quads = c->quads;
+        a.depth = depth;
+        a.rho_ref = d_ref;
+        a.E = c->E;
+        a.eb = c->eb;
+        a.cap = c->cap;
+        a.W = c->W;
+        a.H = c->H;
+        a.G = c->G;
+        a.scale = rp->scale;
+        a.Wi = (int32_t)Wi;
+        a.Hi = (int32_t)Hi;
+        a.tau1 = (unsigned long long)std::llround(-std::log1p(-(double)rp->alpha) * 1048576.0);
+        a.width_min = rp->width_min;
+        a.width_max = rp->width_max;
+        a.log_width = rp->log_width;
+        int n_sm = 0;
+        e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device);
+        if (e == cudaSuccess)
+            e = launch_render(c->p.rho_dtype, a, c->rho, (int64_t)c->G * c->H * c->W,
+                              !(rp->rho_ref > 0.0f), n_sm, c->stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_render_resolve(depth, c->G, npx, d_pal, rp->background, d_rgba, d_acc,
+                                  c->stream);
+    if (e == cudaSuccess && !dev)
+        e = cudaMemcpyAsync(rgba, d_rgba, (size_t)npx * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && !dev && accum)
+        e = cudaMemcpyAsync(accum, d_acc, (size_t)npx * 32, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess)
+        return fail(&c->err, e == cudaErrorMemoryAllocation ? BUNDLE_ENOMEM : BUNDLE_ECUDA,
+                    "bundle_render: %s", cudaGetErrorString(e));
+    return BUNDLE_OK;
+}
+
 bundle_status bundle_sync(bundle_ctx* c) {
     if (!c) return BUNDLE_EINVAL;
     DeviceGuard dg(c->device);

@@ -60,6 +60,22 @@ struct StepArgs {
     unsigned long long* mass;  // total weight splatted by this launch (segment mode)
 };
 
+struct RenderArgs {
+    const int32_t* cnt;      // [E] points per slot of the current polylines
+    const float2* pts;       // current polylines (block layout)
+    const int32_t* group;    // [E] per slot
+    const int32_t* weight;   // [E] per slot
+    const void* quads;       // density quads of the last iteration (rho type)
+    unsigned long long* depth;  // [G][Hi][Wi]: optical depth per bin (2^-20 units)
+    unsigned int* rho_ref;   // density mapped to the full width, as float bits
+    int64_t E;
+    int32_t eb, cap, W, H, G;
+    int32_t scale, Wi, Hi;   // image = grid x scale
+    unsigned long long tau1; // optical depth of one unit-weight edge, 2^-20 units
+    float width_min, width_max;
+    int32_t log_width;
+};
+
 struct FilterArgs {
     const uint32_t* hist;  // [copies][G][H][W]: the histogram is the sum of the copies
     int32_t hist_copies;
@@ -95,6 +111,13 @@ cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cud
 cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st);
 // Fold histogram copies 1.. into copy 0 (their sum is unchanged), n cells per copy.
 cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t st);
+// Renderer: capsule fragments into the accumulators (after the stack maximum of rho
+// into *rho_ref when want_max), then the RGBA8 resolve.
+cudaError_t launch_render(int rho_dtype, const RenderArgs& a, const void* rho, int64_t rho_n,
+                          bool want_max, int n_sm, cudaStream_t st);
+cudaError_t launch_render_resolve(const unsigned long long* depth, int G, int64_t n_pixels,
+                                  const int32_t* palette, const unsigned char* bg, void* rgba,
+                                  void* accum, cudaStream_t st);
 // Ink statistics of the histogram into stats[2 * (*iter)] (skipped past stats_cap).
 cudaError_t launch_ink(const uint32_t* hist, int64_t cells, int G, int copies,
                        unsigned long long* stats, const int32_t* iter, int32_t stats_cap,
