@@ -500,6 +500,15 @@ def run_batch(args):
                   weight=w.weight) for w in ws]
     clocks = ClockSampler(torch.cuda.current_device())
     b = pkg.bundle_init_batch(descs, ps, stream=stream)
+    # tile shapes measured per graph on its own edges (same results whatever they are)
+    t_tune = time.perf_counter()
+    pkg.bundle_autotune(b)
+    t_tune = time.perf_counter() - t_tune
+    tiles = {}
+    for k in range(pkg.bundle_batch_size(b)):
+        inf = pkg.bundle_get_info(pkg.bundle_batch_member(b, k))
+        key = f"eb{inf.tile_eb}/row{inf.tile_row}/strip{inf.tile_strip}"
+        tiles[key] = tiles.get(key, 0) + 1
     pkg.bundle_iterate(b, args.warmup)
     pkg.bundle_sync(b)
     d0 = pkg.bundle_get_info(b).points_processed
@@ -512,6 +521,19 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     upd = pkg.bundle_get_info(b).points_processed - d0
+    pkg.bundle_destroy(b)
+    # the same batch with the size-heuristic tiles
+    b = pkg.bundle_init_batch(descs, ps, stream=stream)
+    pkg.bundle_iterate(b, args.warmup)
+    pkg.bundle_sync(b)
+    h0 = pkg.bundle_get_info(b).points_processed
+    torch.cuda.synchronize()
+    t0.record(stream)
+    pkg.bundle_iterate(b, args.steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    heur_ms = t0.elapsed_time(t1)
+    heur_upd = pkg.bundle_get_info(b).points_processed - h0
     pkg.bundle_destroy(b)
     # the same graphs, one plain context at a time
     seq_ms, seq_upd = 0.0, 0
@@ -541,6 +563,9 @@ def run_batch(args):
                                 "10k-500k), 1-16 groups, grids 256^2/512^2/1024^2, r 4-12, "
                                 "k=3, <= 64 samples/edge"), "graphs": len(ws), "edges": E,
                    "points_per_step": upd / args.steps, "rho_dtype": args.rho},
+        "autotune": {"seconds": t_tune, "tiles": tiles,
+                     "untuned_batch": {"value": heur_upd / (heur_ms / 1e3),
+                                       "ms_per_step": heur_ms / args.steps}},
         "sequential": {"value": seq_upd / (seq_ms / 1e3), "ms_per_step": seq_ms / args.steps,
                        "speedup_of_batch": (upd / ms) / (seq_upd / seq_ms)},
         "clocks": clk,

@@ -104,6 +104,10 @@ typedef struct {
     int64_t device_bytes;       /* device memory owned by the context */
     int64_t points_processed;   /* sample points resampled and splatted since init: the sum
                                    over iterations of the points each iteration advects */
+    int32_t tile_eb;            /* edges per block of the point kernels */
+    int32_t tile_row;           /* row-pass variant: 0 by width, 1 register rows, 2 shared rows */
+    int32_t tile_strip;         /* column-pass strip: 0 by height, else 2, 4 or 8 columns */
+    int32_t reserved;
 } bundle_info;
 
 typedef struct bundle_ctx bundle_ctx;
@@ -283,6 +287,27 @@ typedef struct {
 bundle_status bundle_render(bundle_ctx* ctx, const bundle_render_params* params,
                             const uint8_t* palette, uint8_t* rgba, int64_t* accum,
                             int32_t flags);
+
+/*
+ * Autotuner for the tile shapes (the paper has no counterpart; its CPU threads need
+ * none). On a context fresh from bundle_init (or a batch of them, each graph tuned on
+ * its own edges), times on the GPU: the edges per block of the point kernels (16, 32,
+ * 64, 128; each candidate resamples, splats and filters the straight edges, then
+ * the fused advect + resample step is timed), the row-pass variant and the column-pass
+ * strip, and keeps the fastest of each (bundle_info.tile_*). Results do not depend on
+ * the tiles: every choice gives the same bits. The context returns to its fresh state
+ * (iteration 0). ESTATE after an iteration, for bundle_init_polylines contexts and for
+ * batch members; synchronises the stream; allocates E * 32 bytes while it runs.
+ */
+bundle_status bundle_autotune(bundle_ctx* ctx);
+
+/* Set the tiles by hand (e.g. those an earlier bundle_autotune chose for the same
+ * shape): eb 0 (keep) or 16, 32, 64, 128 -- only on a fresh bundle_init context;
+ * row_mode 0 (by width), 1 (register rows, widths of 225..256, 481..512 or 993..1024
+ * cells), 2 (shared-memory rows); col_strip 0 (by height), 2, 4 or 8 (when the strip's
+ * column fits in shared memory). EINVAL for a choice that does not exist, ESTATE for
+ * eb on an iterated context or for batches. */
+bundle_status bundle_set_tiles(bundle_ctx* ctx, int32_t eb, int32_t row_mode, int32_t col_strip);
 
 /* Sizes, widths, map, schedule and point counts of a context (synchronises the stream).
  * For a batch: sums of the counts over its graphs; sizes and map of graph 0. */

@@ -38,7 +38,8 @@ EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bu
             "bundle_destroy", "bundle_last_error", "bundle_status_string",
             "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc",
             "bundle_init_batch", "bundle_batch_size", "bundle_batch_member",
-            "bundle_set_interaction", "bundle_fetch_ink", "bundle_render")
+            "bundle_set_interaction", "bundle_fetch_ink", "bundle_render", "bundle_autotune",
+            "bundle_set_tiles")
 
 
 class BundleParams(ctypes.Structure):
@@ -66,6 +67,8 @@ class BundleInfo(ctypes.Structure):
         ("sum_bits", ctypes.c_int32), ("rho_dtype", ctypes.c_int32),
         ("iteration", ctypes.c_int32), ("map", ctypes.c_double * 5), ("h_next", ctypes.c_double),
         ("device_bytes", ctypes.c_int64), ("points_processed", ctypes.c_int64),
+        ("tile_eb", ctypes.c_int32), ("tile_row", ctypes.c_int32), ("tile_strip", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -143,6 +146,10 @@ def lib():
     L.bundle_batch_member.argtypes = [P, i32]
     L.bundle_batch_member.restype = P
     L.bundle_set_interaction.argtypes = [P, P, i64]
+    L.bundle_set_tiles.argtypes = [P, i32, i32, i32]
+    L.bundle_set_tiles.restype = i32
+    L.bundle_autotune.argtypes = [P]
+    L.bundle_autotune.restype = i32
     L.bundle_render.argtypes = [P, ctypes.POINTER(BundleRenderParams), P, P, P, i32]
     L.bundle_render.restype = i32
     L.bundle_fetch_ink.argtypes = [P, P, i32, i32]
@@ -285,6 +292,16 @@ def bundle_fetch_ink(ctx, first: int, n: int) -> np.ndarray:
     out = np.zeros((max(int(n), 0), 2), np.int64)
     _check(lib().bundle_fetch_ink(ctx, _ptr(out), int(first), int(n)), ctx)
     return out
+
+
+def bundle_autotune(ctx):
+    """Time the tile shapes on this (fresh) context or batch and keep the fastest."""
+    _check(lib().bundle_autotune(ctx), ctx)
+
+
+def bundle_set_tiles(ctx, eb: int = 0, row_mode: int = 0, col_strip: int = 0):
+    """Choose the tile shapes by hand (0 keeps eb / picks row and strip by grid size)."""
+    _check(lib().bundle_set_tiles(ctx, int(eb), int(row_mode), int(col_strip)), ctx)
 
 
 def bundle_iterate(ctx, n_iters: int):

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <new>
 #include <string>
@@ -24,6 +25,9 @@ struct bundle_ctx {
     int32_t cap = 0;
     int32_t eb = kEdgesPerBlock;  // edges per block of the point layout
     int64_t n_blocks = 0;
+    int32_t col_strip = 0;        // column-pass strip (0: by height), set by the autotuner
+    int32_t row_mode = 0;         // row-pass variant (0: by width), set by the autotuner
+    bool straight = false;        // points are the straight edges of bundle_init (2 per slot)
     int32_t sum_bits = 64;
     int64_t mix_self = 1, mix_all = 0;
     float den_f = 1.0f;
@@ -360,7 +364,9 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     while (eb > 8 && E < (int64_t)eb * 152 * 4) eb /= 2;
     c->eb = eb;
     c->n_blocks = (E + eb - 1) / eb;
-    const size_t region = (size_t)c->n_blocks * eb * c->cap;
+    // sized for blocks of kEdgesPerBlock whatever eb is, so that the autotuner can move the
+    // points to any power-of-two block size without reallocating
+    const size_t region = (size_t)((E + kEdgesPerBlock - 1) / kEdgesPerBlock) * kEdgesPerBlock * c->cap;
     const size_t C = (size_t)c->G * c->H * c->W;
     const size_t sb = c->sum_bits / 8;
     CUDA_TRY(e, dalloc(c, &c->perm, E));
@@ -577,6 +583,8 @@ bundle_status run_filter(bundle_ctx* c) {
     f.mix_self = c->mix_self;
     f.mix_all = c->mix_all;
     f.den_f = c->den_f;
+    f.strip = c->col_strip;
+    f.row_mode = c->row_mode;
     if (c->ink)
         CUDA_TRY(&c->err, launch_ink(c->hist, (int64_t)c->H * c->W, c->G, kHistCopies, c->ink,
                                      c->d_iter, BUNDLE_INK_STATS_CAP, c->n_sm, c->stream));
@@ -760,6 +768,7 @@ bundle_status bundle_init(bundle_ctx** out, const bundle_params* p, int64_t n_ed
                          "init staging: %s", cudaGetErrorString(err)));
     c->cur_P = 0;
     c->cur_R = -1;
+    c->straight = true;
     *out = c;
     return BUNDLE_OK;
 }
@@ -1079,6 +1088,269 @@ bundle_ctx* bundle_batch_member(bundle_ctx* c, int32_t k) {
     return c->members[(size_t)k];
 }
 
+// ---------------------------------------------------------------- autotuner
+// Elapsed milliseconds of fn() on the context's stream (events around it).
+static bundle_status time_ms(bundle_ctx* c, const std::function<bundle_status()>& fn, float* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+    bundle_status s = e == cudaSuccess ? fn() : BUNDLE_ECUDA;
+    if (s == BUNDLE_OK && e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (s == BUNDLE_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (s == BUNDLE_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s != BUNDLE_OK) return s;
+    CUDA_TRY(&c->err, e);
+    return BUNDLE_OK;
+}
+
+// Probe state of one fresh context: its straight edges in slot order (two points per
+// slot), from which any block layout can be rebuilt.
+struct TuneProbe {
+    float2* keep = nullptr;
+    TuneProbe() = default;
+    TuneProbe(const TuneProbe&) = delete;
+    TuneProbe& operator=(const TuneProbe&) = delete;
+    ~TuneProbe() { cudaFree(keep); }
+};
+
+static bundle_status probe_begin(bundle_ctx* c, TuneProbe* t) {
+    if (!c->straight || c->iteration != 0 || c->cur_R >= 0)
+        return fail(&c->err, BUNDLE_ESTATE,
+                    "bundle_autotune: needs a context fresh from bundle_init (no iteration yet)");
+    bundle_status s = ensure_schedule(c, 2);
+    if (s != BUNDLE_OK) return s;
+    CUDA_TRY(&c->err, cudaMalloc(&t->keep, (size_t)c->E * 2 * sizeof(float2)));
+    CUDA_TRY(&c->err, launch_relayout_pairs(c->pts[c->cur_P], c->eb, c->cap, t->keep, 1, 2,
+                                            nullptr, c->E, c->stream));
+    return BUNDLE_OK;
+}
+
+// Lay the straight edges out in blocks of eb edges (buffer 0).
+static bundle_status probe_layout(bundle_ctx* c, const TuneProbe& t, int32_t eb) {
+    c->eb = eb;
+    c->n_blocks = (c->E + eb - 1) / eb;
+    CUDA_TRY(&c->err, launch_relayout_pairs(t.keep, 1, 2, c->pts[0], eb, c->cap, c->cnt[0], c->E,
+                                            c->stream));
+    return BUNDLE_OK;
+}
+
+// Iteration 0 up to the density (resample + splat the straight edges, filter), then the
+// fused advect + resample step that is timed: the two halves, enqueued on c->stream.
+static bundle_status probe_prefix(bundle_ctx* c) {
+    CUDA_TRY(&c->err, launch_set_iter(c->d_iter, 0, c->stream));
+    bundle_status s = run_step(c, kModeResample, 0, 1);
+    return s == BUNDLE_OK ? run_filter(c) : s;
+}
+static bundle_status probe_step(bundle_ctx* c) { return run_step(c, kModeAdvectResample, 1, 0); }
+
+// Row-pass variant and column-pass strip of one context, timed on its current
+// histogram (best of three each).
+static bundle_status tune_filter(bundle_ctx* c) {
+    const int sb = c->sum_bits / 8;
+    int best_row = c->row_mode, best_strip = c->col_strip;
+    float best_row_ms = 3.4e38f, best_col_ms = 3.4e38f;
+    FilterArgs f{};
+    f.hist = c->hist;
+    f.hist_copies = kHistCopies;
+    f.Y = c->Y;
+    f.S = c->S;
+    f.G = c->G;
+    f.H = c->H;
+    f.W = c->W;
+    f.r = c->p.radius;
+    f.passes = c->p.passes;
+    bundle_status s;
+    for (int mode = 1; mode <= 2; ++mode) {
+        if (!rowbox_mode_valid(mode, c->W)) continue;
+        f.row_mode = mode;
+        for (int rep = 0; rep < 3; ++rep) {
+            float ms = 0;
+            s = time_ms(c, [&] {
+                return launch_rowbox(c->sum_bits, f, c->stream) == cudaSuccess ? BUNDLE_OK : BUNDLE_ECUDA;
+            }, &ms);
+            if (s != BUNDLE_OK) return s;
+            if (ms < best_row_ms) {
+                best_row_ms = ms;
+                best_row = mode;
+            }
+        }
+    }
+    for (int strip = 2; strip <= 8; strip *= 2) {
+        if (!colbox_strip_valid(strip, c->H, c->p.radius, sb)) continue;
+        f.strip = strip;
+        for (int rep = 0; rep < 3; ++rep) {
+            float ms = 0;
+            s = time_ms(c, [&] {
+                return launch_colbox(c->sum_bits, f, c->stream) == cudaSuccess ? BUNDLE_OK : BUNDLE_ECUDA;
+            }, &ms);
+            if (s != BUNDLE_OK) return s;
+            if (ms < best_col_ms) {
+                best_col_ms = ms;
+                best_strip = strip;
+            }
+        }
+    }
+    c->row_mode = best_row;
+    c->col_strip = best_strip;
+    return BUNDLE_OK;
+}
+
+// Back to the state bundle_init leaves, with the straight edges in blocks of eb.
+static bundle_status probe_end(bundle_ctx* c, const TuneProbe& t, int32_t eb) {
+    bundle_status s = probe_layout(c, t, eb);
+    if (s != BUNDLE_OK) return s;
+    const size_t C = (size_t)c->G * c->H * c->W;
+    CUDA_TRY(&c->err, cudaMemsetAsync(c->hist, 0, C * kHistCopies * sizeof(uint32_t), c->stream));
+    CUDA_TRY(&c->err, cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream));
+    CUDA_TRY(&c->err, cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream));
+    if (c->ink)
+        CUDA_TRY(&c->err, cudaMemsetAsync(c->ink, 0, 2 * sizeof(unsigned long long) *
+                                                         BUNDLE_INK_STATS_CAP, c->stream));
+    CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    c->cur_P = 0;
+    c->cur_R = -1;
+    c->have_density = false;
+    c->ev_used = 0;
+    c->ev_kind.clear();
+    for (cudaGraphExec_t& g : c->gexec)  // captured with the old tiles
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return BUNDLE_OK;
+}
+
+// One graph: every eb candidate lays the straight edges out again, resamples, splats and
+// filters them, and the fused step is timed (best of two); then the filter tiles.
+static bundle_status autotune_one(bundle_ctx* c) {
+    DeviceGuard dg(c->device);
+    TuneProbe t;
+    bundle_status s = probe_begin(c, &t);
+    if (s != BUNDLE_OK) return s;
+    int32_t best_eb = c->eb;
+    float best = 3.4e38f;
+    for (int32_t eb = 16; eb <= kEdgesPerBlock; eb *= 2) {
+        for (int rep = 0; rep < 2; ++rep) {
+            if ((s = probe_layout(c, t, eb)) != BUNDLE_OK || (s = probe_prefix(c)) != BUNDLE_OK)
+                return s;
+            float ms = 0;
+            if ((s = time_ms(c, [&] { return probe_step(c); }, &ms)) != BUNDLE_OK) return s;
+            if (ms < best) {
+                best = ms;
+                best_eb = eb;
+            }
+        }
+    }
+    if ((s = tune_filter(c)) != BUNDLE_OK) return s;
+    return probe_end(c, t, best_eb);
+}
+
+// A batch runs its graphs side by side, so the block size is chosen for the whole batch:
+// each policy (every graph at its size rule, or every graph at 16, 32, 64 or 128 edges
+// per block) times the fused step of all graphs together, forked from the batch stream
+// and joined back (best of two). The filter tiles are then tuned per graph.
+static bundle_status autotune_batch(bundle_ctx* c) {
+    DeviceGuard dg(c->device);
+    const size_t n = c->members.size();
+    std::vector<TuneProbe> t(n);
+    std::vector<int32_t> rule(n);
+    bundle_status s;
+    for (size_t k = 0; k < n; ++k) {
+        if ((s = probe_begin(c->members[k], &t[k])) != BUNDLE_OK)
+            return fail(&c->err, s, "graph %zu: %s", k, c->members[k]->err.c_str());
+        rule[k] = c->members[k]->eb;
+    }
+    int best_policy = 0;
+    float best = 3.4e38f;
+    for (int policy = 0; policy <= 4; ++policy) {  // 0: size rule, 1..4: 16 << (policy - 1)
+        for (int rep = 0; rep < 2; ++rep) {
+            for (size_t k = 0; k < n; ++k) {
+                bundle_ctx* m = c->members[k];
+                const int32_t eb = policy == 0 ? rule[k] : (16 << (policy - 1));
+                if ((s = probe_layout(m, t[k], eb)) != BUNDLE_OK || (s = probe_prefix(m)) != BUNDLE_OK)
+                    return s;
+            }
+            for (bundle_ctx* m : c->members) CUDA_TRY(&c->err, cudaStreamSynchronize(m->stream));
+            float ms = 0;
+            s = time_ms(c, [&] {
+                bundle_status r = batch_fork(c, c->stream);
+                for (size_t k = 0; k < n && r == BUNDLE_OK; ++k) r = probe_step(c->members[k]);
+                return r == BUNDLE_OK ? batch_join(c, c->stream) : r;
+            }, &ms);
+            if (s != BUNDLE_OK) return s;
+            if (ms < best) {
+                best = ms;
+                best_policy = policy;
+            }
+        }
+    }
+    for (size_t k = 0; k < n; ++k) {
+        bundle_ctx* m = c->members[k];
+        if ((s = tune_filter(m)) != BUNDLE_OK) return s;
+        const int32_t eb = best_policy == 0 ? rule[k] : (16 << (best_policy - 1));
+        if ((s = probe_end(m, t[k], eb)) != BUNDLE_OK) return s;
+    }
+    for (cudaGraphExec_t& g : c->bexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_set_tiles(bundle_ctx* c, int32_t eb, int32_t row_mode, int32_t col_strip) {
+    if (!c) return BUNDLE_EINVAL;
+    if (!c->members.empty() || c->is_member)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_set_tiles: set the tiles of single contexts");
+    if (eb != 0 && (eb < 16 || eb > kEdgesPerBlock || (eb & (eb - 1)) != 0))
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: eb must be 0, 16, 32, 64 or 128");
+    if (!rowbox_mode_valid(row_mode, c->W))
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: row variant %d does not exist for "
+                    "width %d", row_mode, c->W);
+    if (col_strip != 0 && !colbox_strip_valid(col_strip, c->H, c->p.radius, c->sum_bits / 8))
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: strip %d does not fit height %d",
+                    col_strip, c->H);
+    if (eb != 0 && eb != c->eb) {
+        if (!c->straight || c->iteration != 0 || c->cur_R >= 0)
+            return fail(&c->err, BUNDLE_ESTATE,
+                        "bundle_set_tiles: eb can change only on a context fresh from bundle_init");
+        DeviceGuard dg(c->device);
+        float2* keep = nullptr;
+        CUDA_TRY(&c->err, cudaMalloc(&keep, (size_t)c->E * 2 * sizeof(float2)));
+        cudaError_t e = launch_relayout_pairs(c->pts[c->cur_P], c->eb, c->cap, keep, 1, 2, nullptr,
+                                              c->E, c->stream);
+        if (e == cudaSuccess)
+            e = launch_relayout_pairs(keep, 1, 2, c->pts[0], eb, c->cap, c->cnt[0], c->E, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(keep);
+        CUDA_TRY(&c->err, e);
+        c->eb = eb;
+        c->n_blocks = (c->E + eb - 1) / eb;
+        c->cur_P = 0;
+    }
+    c->row_mode = row_mode;
+    c->col_strip = col_strip;
+    for (cudaGraphExec_t& g : c->gexec)  // captured with the old tiles
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_autotune(bundle_ctx* c) {
+    if (!c) return BUNDLE_EINVAL;
+    if (c->is_member)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_autotune: tune the batch, not its member");
+    if (c->members.empty()) return autotune_one(c);
+    if (c->iteration != 0)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_autotune: the batch has already iterated");
+    return autotune_batch(c);
+}
+
 // Deferred device-side errors (segment histogram overflow). Synchronises the stream.
 static bundle_status check_device_flag(bundle_ctx* c) {
     if (!c->d_flag) return BUNDLE_OK;
@@ -1359,6 +1631,9 @@ bundle_status bundle_get_info(const bundle_ctx* c, bundle_info* out) {
     std::memcpy(out->map, c->map, sizeof c->map);
     out->h_next = bandwidth(c->p, c->iteration);
     out->device_bytes = c->device_bytes;
+    out->tile_eb = c->eb;
+    out->tile_row = c->row_mode;
+    out->tile_strip = c->col_strip;
     unsigned long long tot[2] = {0, 0};
     int sels[2] = {c->cur_P, c->cur_R};
     for (int k = 0; k < 2; ++k) {

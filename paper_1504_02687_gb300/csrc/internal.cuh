@@ -89,6 +89,8 @@ struct FilterArgs {
     int64_t mix_all;       // p : weight of the all-groups sum
     float inv_den_f;       // unused (kept for a future reciprocal form)
     float den_f;           // q (G - 1) s^k (or s^k for one group), rounded to float
+    int32_t strip;         // column-pass strip width 2, 4 or 8 (0: by height)
+    int32_t row_mode;      // row pass: 0 by width, 1 register-resident rows, 2 shared-memory rows
 };
 
 // Density quads. The gather side of the iteration reads the density through a
@@ -151,6 +153,14 @@ cudaError_t launch_sum_counts(const int32_t* cnt, int64_t E, unsigned long long*
                               cudaStream_t st);
 // Device iteration counter used with the device schedule of h (graph-friendly).
 cudaError_t launch_set_iter(int32_t* iter, int32_t value, cudaStream_t st);
+// Copy two-point polylines (the straight edges of a fresh context) from one block layout
+// to another: slot s sits at (s / eb) * eb * cap + 2 * (s % eb); cnt_dst (if set) gets 2.
+cudaError_t launch_relayout_pairs(const float2* src, int32_t eb_src, int32_t cap_src, float2* dst,
+                                  int32_t eb_dst, int32_t cap_dst, int32_t* cnt_dst, int64_t E,
+                                  cudaStream_t st);
+// Whether a row-pass / column-pass tile choice exists for this grid.
+bool rowbox_mode_valid(int mode, int W);
+bool colbox_strip_valid(int strip, int H, int r, int sum_bytes);
 // Sticky overflow flag: set when *mass > allowed.
 cudaError_t launch_check_mass(const unsigned long long* mass, unsigned long long allowed,
                               int32_t* flag, cudaStream_t st);

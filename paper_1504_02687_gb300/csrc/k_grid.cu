@@ -319,9 +319,11 @@ template <typename TS>
 cudaError_t rowbox_t(const FilterArgs& a, cudaStream_t st) {
     const int c = (a.W + 31) / 32;
     const int pad = (c % 2 == 0) ? 1 : 2;
-    if (c == 32) return rowbox_reg_t<TS, 32>(a, st);
-    if (c == 16) return rowbox_reg_t<TS, 16>(a, st);
-    if (c == 8) return rowbox_reg_t<TS, 8>(a, st);
+    if (a.row_mode != 2) {  // register-resident rows where a template exists for the width
+        if (c == 32) return rowbox_reg_t<TS, 32>(a, st);
+        if (c == 16) return rowbox_reg_t<TS, 16>(a, st);
+        if (c == 8) return rowbox_reg_t<TS, 8>(a, st);
+    }
     const size_t per_row = (size_t)2 * (a.W + 32 * pad) * sizeof(TS);
     size_t fit = (200u * 1024u) / per_row;
     int rows = (int)(fit < 4 ? fit : 4);
@@ -356,8 +358,9 @@ cudaError_t colbox_strip(const FilterArgs& a, cudaStream_t st) {
 
 template <typename TS>
 cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
-    if (a.H <= 1024) return colbox_strip<TS, 8>(a, st);
-    if (a.H <= 2048) return colbox_strip<TS, 4>(a, st);
+    const int strip = a.strip ? a.strip : (a.H <= 1024 ? 8 : a.H <= 2048 ? 4 : 2);
+    if (strip == 8) return colbox_strip<TS, 8>(a, st);
+    if (strip == 4) return colbox_strip<TS, 4>(a, st);
     return colbox_strip<TS, 2>(a, st);
 }
 
@@ -395,6 +398,20 @@ cudaError_t combine_t(const FilterArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+bool rowbox_mode_valid(int mode, int W) {
+    const int c = (W + 31) / 32;
+    if (mode == 1) return c == 8 || c == 16 || c == 32;
+    return mode == 0 || mode == 2;
+}
+
+bool colbox_strip_valid(int strip, int H, int r, int sum_bytes) {
+    const int nch = (H + kChunk - 1) / kChunk;
+    const int ntab = H + 2 * r + 2;
+    const size_t smem = (size_t)(H + nch) * strip * sum_bytes + (size_t)(ntab + ntab / kChunk + 1) * 4;
+    return (strip == 2 || strip == 4 || strip == 8) && strip * nch <= kColThreads &&
+           smem <= (size_t)227 * 1024;
+}
 
 cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
     return sum_bits == 32 ? rowbox_t<uint32_t>(a, st) : rowbox_t<unsigned long long>(a, st);

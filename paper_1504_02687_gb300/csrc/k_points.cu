@@ -551,6 +551,17 @@ __global__ void k_sum_counts(const int32_t* __restrict__ cnt, int64_t E,
 }
 
 __global__ void k_set_iter(int32_t* iter, int32_t value) { *iter = value; }
+__global__ void k_relayout_pairs(const float2* __restrict__ src, int32_t eb_src, int32_t cap_src,
+                                 float2* __restrict__ dst, int32_t eb_dst, int32_t cap_dst,
+                                 int32_t* cnt_dst, int64_t E) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E) return;
+    const int64_t i = (s / eb_src) * eb_src * cap_src + 2 * (s % eb_src);
+    const int64_t o = (s / eb_dst) * eb_dst * cap_dst + 2 * (s % eb_dst);
+    dst[o] = src[i];
+    dst[o + 1] = src[i + 1];
+    if (cnt_dst) cnt_dst[s] = 2;
+}
 __global__ void k_check_mass(const unsigned long long* mass, unsigned long long allowed,
                              int32_t* flag) {
     if (*mass > allowed) *flag = 1;
@@ -639,6 +650,15 @@ cudaError_t launch_layout_to_caller(const int32_t* perm, const int32_t* cnt, con
 
 cudaError_t launch_set_iter(int32_t* iter, int32_t value, cudaStream_t st) {
     k_set_iter<<<1, 1, 0, st>>>(iter, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout_pairs(const float2* src, int32_t eb_src, int32_t cap_src, float2* dst,
+                                  int32_t eb_dst, int32_t cap_dst, int32_t* cnt_dst, int64_t E,
+                                  cudaStream_t st) {
+    if (E <= 0) return cudaSuccess;
+    k_relayout_pairs<<<(unsigned)((E + 255) / 256), 256, 0, st>>>(src, eb_src, cap_src, dst, eb_dst,
+                                                                  cap_dst, cnt_dst, E);
     return cudaGetLastError();
 }
 

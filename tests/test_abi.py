@@ -65,7 +65,8 @@ def test_struct_mirrors_match_the_c_layout(tmp_path):
 
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     pairs = (("bundle_params", pkg.BundleParams), ("bundle_info", pkg.BundleInfo),
-             ("bundle_graph_desc", pkg.BundleGraphDesc))
+             ("bundle_graph_desc", pkg.BundleGraphDesc),
+             ("bundle_render_params", pkg.BundleRenderParams))
     for cname, cls in pairs:
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:

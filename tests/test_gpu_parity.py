@@ -378,6 +378,86 @@ def test_optimised_step_converges_in_fewer_iterations():
     assert np.flatnonzero(opt <= fix[-1])[0] <= 8
 
 
+def _state(ctx):
+    off, xy = pkg.bundle_fetch(ctx, pixels=True)
+    return [off, xy] + [pkg.bundle_fetch_density(ctx, k) for k in
+                        (pkg.DENSITY_HIST, pkg.DENSITY_SUMS, pkg.DENSITY_RHO)]
+
+
+def test_every_tile_choice_gives_the_same_bits():
+    """Edges per block, row-pass variant and column-pass strip change only the schedule: after
+    3 iterations (graph path included) every combination equals the default bit for bit."""
+    w = synth.tiny(seed=21, n_edges=900, n_groups=3, grid=(256, 240), radius=5, passes=3,
+                   n_fixed=0, n_max=32, weighted=True)
+    p = params_for(w)
+    ref = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    try:
+        pkg.bundle_iterate(ref, 3)
+        expect = _state(ref)
+    finally:
+        pkg.bundle_destroy(ref)
+    for eb in (16, 32, 64, 128):
+        for row in (1, 2):
+            for strip in (2, 4, 8):
+                ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+                try:
+                    pkg.bundle_set_tiles(ctx, eb, row, strip)
+                    info = pkg.bundle_get_info(ctx)
+                    assert (info.tile_eb, info.tile_row, info.tile_strip) == (eb, row, strip)
+                    pkg.bundle_iterate(ctx, 3)
+                    for a, b in zip(_state(ctx), expect):
+                        np.testing.assert_array_equal(a, b)
+                finally:
+                    pkg.bundle_destroy(ctx)
+
+
+def test_autotune_keeps_results_and_states():
+    w = synth.tiny(seed=22, n_edges=1200, n_groups=2, grid=(256, 256), radius=4, passes=3,
+                   n_fixed=0, n_max=24)
+    p = params_for(w, flags=pkg.FLAG_INK_STATS)
+    a = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    b = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    try:
+        pkg.bundle_autotune(b)
+        info = pkg.bundle_get_info(b)
+        print("autotuned tiles:", info.tile_eb, info.tile_row, info.tile_strip)
+        assert info.iteration == 0 and info.points_processed == 0
+        assert info.tile_eb in (16, 32, 64, 128) and info.tile_strip in (2, 4, 8)
+        pkg.bundle_iterate(a, 4)
+        pkg.bundle_iterate(b, 4)
+        for x, y in zip(_state(a), _state(b)):
+            np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(pkg.bundle_fetch_ink(a, 0, 4), pkg.bundle_fetch_ink(b, 0, 4))
+        with pytest.raises(pkg.BundleError) as ei:   # only before the first iteration
+            pkg.bundle_autotune(b)
+        assert ei.value.status == pkg.BUNDLE_ESTATE
+        with pytest.raises(pkg.BundleError) as ei:
+            pkg.bundle_set_tiles(b, 32, 0, 0)
+        assert ei.value.status == pkg.BUNDLE_ESTATE
+    finally:
+        pkg.bundle_destroy(a)
+        pkg.bundle_destroy(b)
+    # a batch tunes each graph on its own edges; results equal the untuned batch
+    ws = [synth.tiny(seed=30 + k, n_edges=n, n_groups=g, grid=(128, 128), radius=3, passes=3)
+          for k, (n, g) in enumerate([(300, 1), (1500, 3), (700, 2)])]
+    descs = [dict(src_xy=x.src_xy, dst_xy=x.dst_xy, group=x.group, n_groups=x.n_groups,
+                  weight=x.weight) for x in ws]
+    ps = [params_for(x) for x in ws]
+    b1 = pkg.bundle_init_batch(descs, ps)
+    b2 = pkg.bundle_init_batch(descs, ps)
+    try:
+        pkg.bundle_autotune(b2)
+        pkg.bundle_iterate(b1, 3)
+        pkg.bundle_iterate(b2, 3)
+        for k in range(len(ws)):
+            for x, y in zip(_state(pkg.bundle_batch_member(b1, k)),
+                            _state(pkg.bundle_batch_member(b2, k))):
+                np.testing.assert_array_equal(x, y)
+    finally:
+        pkg.bundle_destroy(b1)
+        pkg.bundle_destroy(b2)
+
+
 def test_optimised_step_never_lowers_density():
     """Sec. 3.3: the halving step guarantees every advected point a density not lower than
     before; KDEEB's fixed step does not (beta = 0 so the advected points are the output)."""
