@@ -112,7 +112,32 @@ __global__ void __launch_bounds__(32 * kRowWarps)
     if (v >= H) return;
     const size_t base = ((size_t)g * H + v) * W;
     const size_t stride_copy = (size_t)G * H * W;
-    if ((W & 3) == 0) {
+    if ((W & 3) == 0 && copies == 2) {
+        // every 16-byte load of both copies in flight before the first is summed
+        constexpr int kIt = C / 4;  // W <= 32 C: at most C / 4 loads of 4 cells per lane
+        const uint4* h0 = reinterpret_cast<const uint4*>(hist + base);
+        const uint4* h1 = reinterpret_cast<const uint4*>(hist + stride_copy + base);
+        uint4 u[kIt], w[kIt];
+#pragma unroll
+        for (int it = 0; it < kIt; ++it) {
+            const int x4 = lane + 32 * it;
+            if (x4 < (W >> 2)) {
+                u[it] = __ldg(h0 + x4);
+                w[it] = __ldg(h1 + x4);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < kIt; ++it) {
+            const int x4 = lane + 32 * it;
+            if (x4 < (W >> 2)) {
+                const int x = 4 * x4;
+                buf[padded<C>(x)] = (TS)(u[it].x + w[it].x);
+                buf[padded<C>(x + 1)] = (TS)(u[it].y + w[it].y);
+                buf[padded<C>(x + 2)] = (TS)(u[it].z + w[it].z);
+                buf[padded<C>(x + 3)] = (TS)(u[it].w + w[it].w);
+            }
+        }
+    } else if ((W & 3) == 0) {
         const uint4* h0 = reinterpret_cast<const uint4*>(hist + base);
         for (int x4 = lane; x4 < (W >> 2); x4 += 32) {
             uint4 u = __ldg(h0 + x4);
@@ -208,10 +233,35 @@ __global__ void __launch_bounds__(kColThreads)
     const int j = threadIdx.x % STRIP, ch = threadIdx.x / STRIP;
     const size_t lay = (size_t)g * H * W;
     auto prow = [](int row) { return row + row / kChunk; };
-    for (int idx = threadIdx.x; idx < H * STRIP; idx += blockDim.x) {
-        int row = idx / STRIP, col = idx % STRIP, x = x0 + col;
-        buf[prow(row) * STRIP + col] = x < W ? Y[lay + (size_t)row * W + x] : (TS)0;
+    // the strip's rows are copied asynchronously straight into shared memory, all in
+    // flight at once: 16-byte pieces when rows and strips are 16-byte aligned, else one
+    // element per copy; columns past the width are zero-filled
+    constexpr int kPiece = 16 / (int)sizeof(TS);
+    if (STRIP % kPiece == 0 && W % kPiece == 0) {
+        constexpr int kPer = STRIP / kPiece;  // pieces per row of the strip
+        for (int idx = threadIdx.x; idx < H * kPer; idx += blockDim.x) {
+            const int row = idx / kPer, col = (idx % kPer) * kPiece, x = x0 + col;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + prow(row) * STRIP + col);
+            const TS* src = Y + lay + (size_t)row * W + (x < W ? x : 0);
+            const int bytes = x < W ? 16 : 0;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                         "r"(bytes));
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < H * STRIP; idx += blockDim.x) {
+            const int row = idx / STRIP, col = idx % STRIP, x = x0 + col;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + prow(row) * STRIP + col);
+            const TS* src = Y + lay + (size_t)row * W + (x < W ? x : 0);
+            const int bytes = x < W ? (int)sizeof(TS) : 0;
+            if constexpr (sizeof(TS) == 8)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src),
+                             "r"(bytes));
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src),
+                             "r"(bytes));
+        }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     const int i0 = ch * kChunk;
     const int len = max(0, min(kChunk, H - i0));
