@@ -205,13 +205,13 @@ cudaError_t rowbox_reg_t(const FilterArgs& a, cudaStream_t st) {
 
 // --------------------------------------------------------------- column passes
 // One CTA per strip of STRIP columns of one layer, the whole column height in
-// shared memory. Thread (j, ch) owns column j and the 32-row chunk ch; its 32
+// shared memory. Thread (j, ch) owns column j and the 16-row chunk ch; its 16
 // outputs of a pass stay in registers until the whole CTA has read the pass's
 // input. A pad row after every chunk spreads the chunks over the banks. The
 // strip narrows (8, 4, 2 columns) as the height grows so that a CTA keeps 256
 // threads and the strip fits in shared memory.
-constexpr int kChunk = 32;
-constexpr int kColThreads = 256;
+constexpr int kChunk = 16;
+constexpr int kColThreads = 512;
 
 template <typename TS, int STRIP>
 __global__ void __launch_bounds__(kColThreads)

@@ -264,6 +264,43 @@ def test_edge_cases():
             pkg.bundle_destroy(ctx)
 
 
+def test_degenerate_and_maximum_sizes():
+    """Zero-length and duplicate edges; the largest grid (4096^2: the generic row pass and the
+    narrowest column strip) with the largest polylines (64 points); a ragged, odd-sized grid
+    (4093 x 61: element-wise copies in both filter passes)."""
+    rng = np.random.default_rng(7)
+
+    class Wk:
+        group = weight = None
+
+    E = 500
+    s = rng.uniform(0, 1, (E, 2)).astype(np.float32)
+    d = s.copy()                                  # every edge has zero length ...
+    d[::3] = rng.uniform(0, 1, (len(d[::3]), 2))  # ... except one in three
+    s[100:150] = s[100]                           # 50 duplicates of one edge
+    d[100:150] = d[100]
+    cases = [(s, d, dict(grid_w=96, grid_h=96, radius=3, n_fixed=0, n_max=16)),
+             (rng.uniform(0, 1, (2000, 2)).astype(np.float32),
+              rng.uniform(0, 1, (2000, 2)).astype(np.float32),
+              dict(grid_w=4096, grid_h=4096, radius=4, passes=3, n_fixed=64)),
+             (rng.uniform(0, 1, (1500, 2)).astype(np.float32),
+              rng.uniform(0, 1, (1500, 2)).astype(np.float32),
+              dict(grid_w=4093, grid_h=61, radius=5, passes=3, n_fixed=0, n_max=64))]
+    for src, dst, over in cases:
+        p = pkg.default_params(**over)
+        ctx = pkg.bundle_init(p, src, dst)
+        try:
+            _lockstep_once(ctx, Wk, p, max_bad_frac=0.01)
+            _lockstep_once(ctx, Wk, p, max_bad_frac=0.01)
+            off, xy = pkg.bundle_fetch(ctx, pixels=True)
+            n = np.diff(off)
+            zero = np.flatnonzero((src == dst).all(axis=1))
+            if len(zero) and p.n_fixed == 0:
+                assert (n[zero] == 2).all()        # L = 0: two points, both on the source
+        finally:
+            pkg.bundle_destroy(ctx)
+
+
 def test_device_inputs_and_outputs():
     w = synth.tiny(**WORKLOADS["g1-fixed32"])
     p = params_for(w)

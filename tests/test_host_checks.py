@@ -49,6 +49,14 @@ def test_invalid_arguments(pkg, override, needle):
     assert needle in str(ei.value)
 
 
+def test_empty_input_is_rejected(pkg):
+    """No edges: EINVAL before any CUDA call (there is nothing to bundle)."""
+    e = np.zeros((0, 2), np.float32)
+    with pytest.raises(pkg.BundleError, match="n_edges") as ei:
+        pkg.bundle_init(pkg.default_params(grid_w=64, grid_h=64), e, e)
+    assert ei.value.status == pkg.BUNDLE_EINVAL
+
+
 def test_invalid_groups_and_weights(pkg):
     src, dst = _edges(10)
     p = pkg.default_params(grid_w=64, grid_h=64)
