@@ -243,16 +243,19 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                     if (j < n) s_cum[q + j] = c;
                     carry = __shfl_sync(0xffffffffu, c, 31);
                 }
-                if (lane == 0) {
-                    const int m = new_count(carry, a);
-                    s_nn[i] = m;
-                    s_sp[i] = __fdiv_rn(carry, (float)(m - 1));
-                }
             }
         }
         __syncthreads();
 
         if (MODE & kModeResample) {
+            // new point counts and spacings, one thread per polyline (the same thread then
+            // reads its count first in the block scan)
+            for (int i = b0 + tid; i < b1; i += kStepThreads) {
+                const float L = s_cum[s_loc[i] - p0 + s_cnt[i] - 1];
+                const int m = new_count(L, a);
+                s_nn[i] = m;
+                s_sp[i] = __fdiv_rn(L, (float)(m - 1));
+            }
             block_scan_excl(s_nn + b0, s_locn + b0, b1 - b0, s_wtot);
             for (int i = b0 + warp; i < b1; i += kWarps) {
                 const int q = s_loc[i] - p0, n = s_cnt[i], m = s_nn[i];
@@ -273,9 +276,13 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                     }
                 }
                 // endpoints are copied; an edge of zero length puts every point on its source
-                for (int j = lane; j < m; j += 32) {
-                    if (j == m - 1) emit(a, hl, ob + j, s_pts[q + n - 1], w);
-                    else if (j == 0 || L == 0.0f) emit(a, hl, ob + j, s_pts[q], w);
+                if (L == 0.0f) {
+                    for (int j = lane; j < m; j += 32)
+                        emit(a, hl, ob + j, j == m - 1 ? s_pts[q + n - 1] : s_pts[q], w);
+                } else if (lane == 0) {
+                    emit(a, hl, ob, s_pts[q], w);
+                } else if (lane == 1) {
+                    emit(a, hl, ob + m - 1, s_pts[q + n - 1], w);
                 }
                 if (L > 0.0f && m > 2) {
                     // interior output j sits at arc length t_j = j * L / (m - 1) on segment s,
