@@ -15,7 +15,9 @@
  * Readings of passages the paper leaves open (each is a parameter or a fixed
  * choice here, listed in the design notes):
  *  - histogram: every sample point adds its edge weight to the cell it falls
- *    in (Eq. 1 / Eq. 3 read as a point splat; the paper rasterised segments);
+ *    in (Eq. 1 / Eq. 3 read as a point splat), or, as an option, every cell
+ *    that the integer Bresenham line of a polyline segment visits (Sec. 4),
+ *    joints counted once;
  *  - smoothing boundary: half-sample symmetric reflection (-1 -> 0, W -> W-1);
  *  - layer interaction applied after smoothing (smoothing is linear, Sec. 3.2);
  *  - gradient: central differences of the reflection-extended density at the
@@ -24,7 +26,9 @@
  *    "until m is zero" becomes a fixed number of halvings;
  *  - Laplacian smoothing: one Jacobi pass with weight beta, endpoints fixed;
  *  - resampling: uniform arc-length spacing with a fixed count or
- *    clamp(ceil(L / delta) + 1, 2, n_max) points.
+ *    clamp(ceil(L / delta) + 1, 2, n_max) points;
+ *  - rendering (Sec. 3.4): capsule segments with a width from the density,
+ *    order-free alpha accumulation as integer optical depth (oracle_render).
  *
  * Pinning: each function is checked by the non-GPU tests against brute force,
  * closed forms or invariants (see tests/test_oracle_*.py). The absolute

@@ -6,7 +6,7 @@ oracle. Integer stages are bit-exact; floating-point stages are within the state
    |rho_gpu - rho| <= 4 ulp(rho) (relative 2^-21);
  - positions in lockstep: 1e-5 of the grid extent, with every larger difference traced to a
    verified near-tie decision (see parity.advect_mismatch);
- - free-running positions: RMS within 1e-4 of the layout extent (spec tolerance), the
+ - free-running positions: RMS within 1e-4 of the layout extent (the stated FP32 tolerance), the
    maximum reported.
 """
 import numpy as np

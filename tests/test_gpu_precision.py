@@ -4,7 +4,8 @@ after 30 iterations of the criteria-driven configuration (lattice pattern, 8 k-m
 8 x 1024^2 stack, r = 12, k = 4, <= 64 samples per edge).
 
 The oracle runs the whole loop in FP64 from the same FP32 start. Because discrete decisions
-amplify ulp-level differences (reading 18), each form is compared with the
+amplify ulp-level differences (the cell a point falls in, the accepted trial, the resampled
+count flip on near-ties), each form is compared with the
 FP64 method's own drift under a +-1 FP32 ulp perturbation of the start. The edge count is
 20,000 by default so the oracle finishes in seconds; PRECISION_EDGES raises it.
 """
