@@ -118,8 +118,8 @@ __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at
                                      int w) {
     a.pts_out[at] = R;
     if (w != 0 && !a.seg_hist) {
-        const int cx = min(max((int)floorf(R.x), 0), a.W - 1);
-        const int cy = min(max((int)floorf(R.y), 0), a.H - 1);
+        const int cx = min(max(__float2int_rd(R.x), 0), a.W - 1);
+        const int cy = min(max(__float2int_rd(R.y), 0), a.H - 1);
         atomicAdd(hl + (size_t)cy * a.W + cx, (unsigned)w);
     }
 }
@@ -289,11 +289,15 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                     // the first with cum[s] > t_j (binary search on the polyline's cum)
                     for (int j = 1 + lane; j < m - 1; j += 32) {
                         const float t = __fmul_rn((float)j, sp);
-                        int lo = 1, hi = n - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (s_cum[q + mid] > t) hi = mid; else lo = mid + 1;
+                        // the last k in [0, n-2] with cum[k] <= t, by six unrolled halvings
+                        // (n <= 64); the segment is k + 1, the first with cum > t
+                        int pos = 0;
+#pragma unroll
+                        for (int step = 32; step > 0; step >>= 1) {
+                            const int c = pos + step;
+                            if (c <= n - 2 && !(s_cum[q + c] > t)) pos = c;
                         }
+                        const int lo = pos + 1;
                         const float c0 = s_cum[q + lo - 1];
                         const float seg = __fsub_rn(s_cum[q + lo], c0);
                         float fr = seg > 0.0f ? __fdividef(__fsub_rn(t, c0), seg) : 0.0f;
