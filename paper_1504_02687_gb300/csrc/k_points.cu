@@ -123,7 +123,6 @@ __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at
         atomicAdd(hl + (size_t)cy * a.W + cx, (unsigned)w);
     }
 }
-constexpr int kRounds = kMaxCap / 32;  // lanes cover a polyline in this many rounds
 
 // One block of eb slots per CTA, staged through shared memory in
 // batches of whole polylines:
@@ -198,51 +197,52 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
             __syncthreads();
         }
 
-        // one warp per polyline: Laplacian, then arc length and new count
+        // one warp per polyline, two consecutive points per lane (j = 2 lane, 2 lane + 1;
+        // a polyline has at most 64 points): Laplacian smoothing, then the arc lengths. The
+        // neighbours across lanes come by shuffles, so a lane writes only its own points.
         for (int i = b0 + warp; i < b1; i += kWarps) {
             const int q = s_loc[i] - p0, n = s_cnt[i];
+            const int j0 = 2 * lane, j1 = j0 + 1;
+            float2 A0 = j0 < n ? s_pts[q + j0] : make_float2(0.0f, 0.0f);
+            float2 A1 = j1 < n ? s_pts[q + j1] : make_float2(0.0f, 0.0f);
             if (MODE & kModeAdvect) {
-                float2 P[kRounds];
-#pragma unroll
-                for (int r = 0; r < kRounds; ++r) {
-                    const int j = lane + 32 * r;
-                    if (j < n) {
-                        float2 A = s_pts[q + j];
-                        if (j > 0 && j < n - 1) {
-                            float2 Ap = s_pts[q + j - 1], An = s_pts[q + j + 1];
-                            A.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.x, An.x),
-                                            __fmul_rn(a.lap_keep, A.x));
-                            A.y = __fmaf_rn(a.lap_half_beta, __fadd_rn(Ap.y, An.y),
-                                            __fmul_rn(a.lap_keep, A.y));
-                        }
-                        P[r] = A;
-                    }
+                // point j0 - 1 is the previous lane's second, j1 + 1 the next lane's first
+                const float lx = __shfl_up_sync(0xffffffffu, A1.x, 1);
+                const float ly = __shfl_up_sync(0xffffffffu, A1.y, 1);
+                const float rx = __shfl_down_sync(0xffffffffu, A0.x, 1);
+                const float ry = __shfl_down_sync(0xffffffffu, A0.y, 1);
+                float2 B0 = A0, B1 = A1;
+                if (j0 > 0 && j0 < n - 1) {
+                    B0.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(lx, A1.x), __fmul_rn(a.lap_keep, A0.x));
+                    B0.y = __fmaf_rn(a.lap_half_beta, __fadd_rn(ly, A1.y), __fmul_rn(a.lap_keep, A0.y));
                 }
-                __syncwarp();
-#pragma unroll
-                for (int r = 0; r < kRounds; ++r) {
-                    const int j = lane + 32 * r;
-                    if (j < n) {
-                        s_pts[q + j] = P[r];
-                        if (!(MODE & kModeResample)) a.pts_out[region + p0 + q + j] = P[r];
-                    }
+                if (j1 < n - 1) {
+                    B1.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(A0.x, rx), __fmul_rn(a.lap_keep, A1.x));
+                    B1.y = __fmaf_rn(a.lap_half_beta, __fadd_rn(A0.y, ry), __fmul_rn(a.lap_keep, A1.y));
                 }
-                if (!(MODE & kModeResample) && lane == 0) a.cnt_out[e0 + i] = n;
-                __syncwarp();
+                A0 = B0;
+                A1 = B1;
+                if (j0 < n) s_pts[q + j0] = A0;
+                if (j1 < n) s_pts[q + j1] = A1;
+                if (!(MODE & kModeResample)) {
+                    if (j0 < n) a.pts_out[region + p0 + q + j0] = A0;
+                    if (j1 < n) a.pts_out[region + p0 + q + j1] = A1;
+                    if (lane == 0) a.cnt_out[e0 + i] = n;
+                }
             }
             if (MODE & kModeResample) {
-                float carry = 0.0f;
-                const int rounds = (n + 31) >> 5;
-#pragma unroll
-                for (int r = 0; r < kRounds; ++r) {
-                    if (r >= rounds) break;
-                    const int j = lane + 32 * r;
-                    float sl = 0.0f;
-                    if (j >= 1 && j < n) sl = seg_len(s_pts[q + j - 1], s_pts[q + j]);
-                    float c = __fadd_rn(warp_scan_incl(sl, lane), carry);
-                    if (j < n) s_cum[q + j] = c;
-                    carry = __shfl_sync(0xffffffffu, c, 31);
-                }
+                // cum[j]: lengths of the segments up to point j, by a warp scan of the lanes'
+                // pair sums
+                const float px = __shfl_up_sync(0xffffffffu, A1.x, 1);
+                const float py = __shfl_up_sync(0xffffffffu, A1.y, 1);
+                const float s0 = (j0 >= 1 && j0 < n) ? seg_len(make_float2(px, py), A0) : 0.0f;
+                const float s1 = j1 < n ? seg_len(A0, A1) : 0.0f;
+                const float incl = warp_scan_incl(__fadd_rn(s0, s1), lane);
+                float ex = __shfl_up_sync(0xffffffffu, incl, 1);
+                if (lane == 0) ex = 0.0f;
+                const float c0 = __fadd_rn(ex, s0);
+                if (j0 < n) s_cum[q + j0] = c0;
+                if (j1 < n) s_cum[q + j1] = __fadd_rn(c0, s1);
             }
         }
         __syncthreads();
@@ -275,40 +275,45 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                         oy = a.dir_amount * ddx / len;
                     }
                 }
-                // endpoints are copied; an edge of zero length puts every point on its source
-                if (L == 0.0f) {
-                    for (int j = lane; j < m; j += 32)
-                        emit(a, hl, ob + j, j == m - 1 ? s_pts[q + n - 1] : s_pts[q], w);
-                } else if (lane == 0) {
-                    emit(a, hl, ob, s_pts[q], w);
-                } else if (lane == 1) {
-                    emit(a, hl, ob + m - 1, s_pts[q + n - 1], w);
-                }
-                if (L > 0.0f && m > 2) {
-                    // interior output j sits at arc length t_j = j * L / (m - 1) on segment s,
-                    // the first with cum[s] > t_j (binary search on the polyline's cum)
-                    for (int j = 1 + lane; j < m - 1; j += 32) {
-                        const float t = __fmul_rn((float)j, sp);
-                        // the last k in [0, n-2] with cum[k] <= t, by six unrolled halvings
-                        // (n <= 64); the segment is k + 1, the first with cum > t
-                        int pos = 0;
+                // two consecutive outputs per lane, j = 2 lane and 2 lane + 1 (m <= 64).
+                // Endpoints are copied; an edge of zero length puts every point on its
+                // source. Interior output j sits at arc length t_j = j * L / (m - 1) on
+                // segment s, the first with cum[s] > t_j: six halvings find it for the first
+                // output, and the second steps on from there.
+                int lo = 1;
 #pragma unroll
-                        for (int step = 32; step > 0; step >>= 1) {
-                            const int c = pos + step;
-                            if (c <= n - 2 && !(s_cum[q + c] > t)) pos = c;
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int j = 2 * lane + h2;
+                    if (j >= m) break;
+                    float2 R;
+                    if (j == m - 1) {
+                        R = s_pts[q + n - 1];
+                    } else if (j == 0 || L == 0.0f) {
+                        R = s_pts[q];
+                    } else {
+                        const float t = __fmul_rn((float)j, sp);
+                        if (h2 == 0) {
+                            int pos = 0;  // the last k in [0, n-2] with cum[k] <= t
+#pragma unroll
+                            for (int step = 32; step > 0; step >>= 1) {
+                                const int c = pos + step;
+                                if (c <= n - 2 && !(s_cum[q + c] > t)) pos = c;
+                            }
+                            lo = pos + 1;
+                        } else {
+                            while (lo < n - 1 && !(s_cum[q + lo] > t)) ++lo;
                         }
-                        const int lo = pos + 1;
                         const float c0 = s_cum[q + lo - 1];
                         const float seg = __fsub_rn(s_cum[q + lo], c0);
                         float fr = seg > 0.0f ? __fdividef(__fsub_rn(t, c0), seg) : 0.0f;
                         fr = fminf(fmaxf(fr, 0.0f), 1.0f);
                         const float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
-                        float2 R = make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr));
+                        R = make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr));
                         if (ox != 0.0f || oy != 0.0f)
                             R = make_float2(clamp_pos(__fadd_rn(R.x, ox), a.W),
                                             clamp_pos(__fadd_rn(R.y, oy), a.H));
-                        emit(a, hl, ob + j, R, w);
                     }
+                    emit(a, hl, ob + j, R, w);
                 }
                 if (a.seg_hist && w != 0) {
                     // segments of the new polyline (its points were written by this warp)
