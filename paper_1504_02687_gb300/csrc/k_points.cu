@@ -15,9 +15,10 @@ namespace {
 // the direction is the bilinear interpolation of central differences at the
 // four surrounding cell centres on the reflection-extended map; the magnitude
 // starts at h and halves until the density is not lower than at x.
-template <typename T>
-__device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, float h,
-                               float eps, int tries, int fixed_step) {
+template <typename T, int KT>
+__device__ __forceinline__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H,
+                                               float h, float eps, int tries_rt, int fixed_step) {
+    const int tries = KT > 0 ? KT : tries_rt;
     Frame f = frame_of(p.x, p.y, W, H);
     const int64_t Wq = W + kQuadPad;
     const int64_t c = (int64_t)(f.b0 + 2) * Wq + (f.a0 + 2);
@@ -25,16 +26,14 @@ __device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, 
     float4 up = load_quad(Q, c - Wq), lf = load_quad(Q, c - 1);
     float4 rt = load_quad(Q, c + 1), dn = load_quad(Q, c + Wq);
     // E(a0,b0) = up.z, E(a0+1,b0) = up.w, E(a0,b0+1) = dn.x, E(a0+1,b0+1) = dn.y
-    float gx00 = __fmul_rn(__fsub_rn(rt.x, lf.x), 0.5f);
-    float gx10 = __fmul_rn(__fsub_rn(rt.y, lf.y), 0.5f);
-    float gx01 = __fmul_rn(__fsub_rn(rt.z, lf.z), 0.5f);
-    float gx11 = __fmul_rn(__fsub_rn(rt.w, lf.w), 0.5f);
-    float gy00 = __fmul_rn(__fsub_rn(dn.x, up.x), 0.5f);
-    float gy10 = __fmul_rn(__fsub_rn(dn.y, up.y), 0.5f);
-    float gy01 = __fmul_rn(__fsub_rn(dn.z, up.z), 0.5f);
-    float gy11 = __fmul_rn(__fsub_rn(dn.w, up.w), 0.5f);
-    float gx = lerp_rn(lerp_rn(gx00, gx10, f.fu), lerp_rn(gx01, gx11, f.fu), f.fv);
-    float gy = lerp_rn(lerp_rn(gy00, gy10, f.fu), lerp_rn(gy01, gy11, f.fu), f.fv);
+    // central differences (E(a+1) - E(a-1)) / 2, interpolated; halving commutes exactly with
+    // the interpolation (a power-of-two scaling), so it is applied once at the end
+    float gx = lerp_rn(lerp_rn(__fsub_rn(rt.x, lf.x), __fsub_rn(rt.y, lf.y), f.fu),
+                       lerp_rn(__fsub_rn(rt.z, lf.z), __fsub_rn(rt.w, lf.w), f.fu), f.fv);
+    float gy = lerp_rn(lerp_rn(__fsub_rn(dn.x, up.x), __fsub_rn(dn.y, up.y), f.fu),
+                       lerp_rn(__fsub_rn(dn.z, up.z), __fsub_rn(dn.w, up.w), f.fu), f.fv);
+    gx = __fmul_rn(gx, 0.5f);
+    gy = __fmul_rn(gy, 0.5f);
     float rho0 = lerp_rn(lerp_rn(up.z, up.w, f.fu), lerp_rn(dn.x, dn.y, f.fu), f.fv);
     // d = g / max(|g|, eps): one reciprocal square root (direction only)
     const float n2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
@@ -43,6 +42,7 @@ __device__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H, 
     if (fixed_step)  // KDEEB's step (Sec. 3.3): magnitude h whatever the density there
         return make_float2(clamp_pos(__fmaf_rn(h, dx, p.x), W), clamp_pos(__fmaf_rn(h, dy, p.y), H));
     float m = h;
+#pragma unroll
     for (int t = 0; t < tries; ++t) {
         float xn = clamp_pos(__fmaf_rn(m, dx, p.x), W);
         float yn = clamp_pos(__fmaf_rn(m, dy, p.y), H);
@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
                 const int j = p0 + k - s_loc[i];
                 if (j > 0 && j < s_cnt[i] - 1) {
                     const T* Q = static_cast<const T*>(a.quads) + (int64_t)s_grp[i] * QC * 4;
-                    s_pts[k] = advect_point(s_pts[k], Q, a.W, a.H, h, a.eps, a.tries, a.fixed_step);
+                    s_pts[k] = a.tries == 8
+                                   ? advect_point<T, 8>(s_pts[k], Q, a.W, a.H, h, a.eps, 8, a.fixed_step)
+                                   : advect_point<T, 0>(s_pts[k], Q, a.W, a.H, h, a.eps, a.tries,
+                                                        a.fixed_step);
                 }
             }
             __syncthreads();
