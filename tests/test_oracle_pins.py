@@ -159,6 +159,28 @@ def test_smooth_variance_closed_form(oracle_mod):
     assert np.abs(prof - gauss).max() < 0.1 * gauss.max()
 
 
+def test_smooth_impulse_approaches_gaussian(oracle_mod):
+    """Sec. 3.1 (repeated averaging filters approximate a Gaussian): the k-pass response to an
+    impulse, normalised by s^k, keeps unit mass and its L2 distance to the Gaussian of
+    sigma^2 = k r (r+1) / 3 shrinks as k grows (central limit), below 8 % from k = 3 on."""
+    r = 4
+    errs = []
+    for k in (1, 2, 3, 4, 6):
+        n = 6 * r * k + 1
+        h = np.zeros((1, n, n), np.int64)
+        c = n // 2
+        h[0, c, c] = 1
+        S = oracle_mod.smooth(h, r, k)[0].astype(float) / float((2 * r + 1) ** (2 * k))
+        assert abs(S.sum() - 1.0) < 1e-12
+        x = np.arange(n) - c
+        g = np.exp(-x ** 2 / (2 * k * r * (r + 1) / 3))
+        g /= g.sum()
+        G = np.outer(g, g)
+        errs.append(np.linalg.norm(S - G) / np.linalg.norm(G))
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert errs[2] < 0.08 and errs[-1] < 0.04
+
+
 def test_smooth_mirror_symmetry(oracle_mod):
     rng = np.random.default_rng(3)
     X = rng.integers(0, 9, (1, 12, 10)).astype(np.int64)
