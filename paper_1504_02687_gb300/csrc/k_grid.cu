@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(kColThreads)
     // flight at once: 16-byte pieces when rows and strips are 16-byte aligned, else one
     // element per copy; columns past the width are zero-filled
     constexpr int kPiece = 16 / (int)sizeof(TS);
+    constexpr int kPer = STRIP % kPiece == 0 ? STRIP / kPiece : 1;  // pieces per row of the strip
     if (STRIP % kPiece == 0 && W % kPiece == 0) {
-        constexpr int kPer = STRIP / kPiece;  // pieces per row of the strip
         for (int idx = threadIdx.x; idx < H * kPer; idx += blockDim.x) {
             const int row = idx / kPer, col = (idx % kPer) * kPiece, x = x0 + col;
             const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + prow(row) * STRIP + col);
