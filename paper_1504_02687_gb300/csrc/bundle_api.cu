@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <limits>
+#include <memory>
 #include <new>
 #include <string>
 #include <thread>
@@ -516,7 +517,8 @@ cudaError_t timed(bundle_ctx* c, int kind, F fn) {
     return e;
 }
 
-bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
+// Arguments of one step launch of context c from buffer `in` to buffer `out`.
+StepArgs make_step_args(bundle_ctx* c, int mode, int in, int out) {
     StepArgs a{};
     a.cnt_in = c->cnt[in];
     a.pts_in = c->pts[in];
@@ -550,6 +552,11 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
     a.dir_amount = (mode == kModeResample && c->iteration == 0)
                        ? (float)((double)c->p.directed_offset * std::max(c->W, c->H))
                        : 0.0f;
+    return a;
+}
+
+bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
+    const StepArgs a = make_step_args(c, mode, in, out);
     if (mode & kModeResample)
         CUDA_TRY(&c->err, timed(c, kProfHistClear, [&] {
                      return cudaMemsetAsync(c->hist, 0,
@@ -932,6 +939,16 @@ static bundle_status batch_join(bundle_ctx* c, cudaStream_t into) {
 }
 
 // One steady-state iteration of every member, each on its own branch, as one graph.
+// The steady iterations of a batch run one step launch over all its graphs when they
+// share the density type and need no per-graph check after the step (the segment
+// histogram's mass check).
+static bool batch_mergeable(const bundle_ctx* c) {
+    for (const bundle_ctx* m : c->members)
+        if (m->p.rho_dtype != c->members[0]->p.rho_dtype || (m->p.flags & BUNDLE_FLAG_SEGMENT_HIST))
+            return false;
+    return true;
+}
+
 static bundle_status build_batch_graph(bundle_ctx* c, int R) {
     if (!c->cap_stream)
         CUDA_TRY(&c->err, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -946,11 +963,41 @@ static bundle_status build_batch_graph(bundle_ctx* c, int R) {
     for (bundle_ctx* m : c->members) saved.push_back(m->stream);
     for (bundle_ctx* m : c->members) m->stream = m->cap_stream;
     if (s == BUNDLE_OK) s = batch_fork(c, c->cap_stream);
-    for (size_t k = 0; k < c->members.size() && s == BUNDLE_OK; ++k) {
-        s = launch_iteration(c->members[k], R);
-        if (s != BUNDLE_OK) c->err = "member " + std::to_string(k) + ": " + c->members[k]->err;
+    if (batch_mergeable(c)) {
+        // every graph's filter on its own branch, then one step launch over all graphs
+        for (size_t k = 0; k < c->members.size() && s == BUNDLE_OK; ++k) {
+            bundle_ctx* m = c->members[k];
+            s = run_filter(m);
+            if (s == BUNDLE_OK &&
+                cudaMemsetAsync(m->hist, 0, (size_t)kHistCopies * m->G * m->H * m->W * sizeof(uint32_t),
+                                m->stream) != cudaSuccess)
+                s = BUNDLE_ECUDA;
+            if (s != BUNDLE_OK) c->err = "member " + std::to_string(k) + ": " + m->err;
+        }
+        if (s == BUNDLE_OK) s = batch_join(c, c->cap_stream);
+        std::unique_ptr<BatchStepArgs> P(new (std::nothrow) BatchStepArgs());
+        if (!P) s = fail(&c->err, BUNDLE_ENOMEM, "host allocation failed");
+        for (size_t k0 = 0; k0 < c->members.size() && s == BUNDLE_OK; k0 += kBatchLaunch) {
+            const size_t n = std::min<size_t>(kBatchLaunch, c->members.size() - k0);
+            P->n = (int32_t)n;
+            P->blk[0] = 0;
+            for (size_t j = 0; j < n; ++j) {
+                bundle_ctx* m = c->members[k0 + j];
+                P->a[j] = make_step_args(m, kModeAdvectResample, R, 1 - R);
+                P->blk[j + 1] = P->blk[j] + (int32_t)((m->E + m->eb - 1) / m->eb);
+            }
+            if (launch_step_batch(kModeAdvectResample, c->members[0]->p.rho_dtype, *P,
+                                  c->cap_stream) != cudaSuccess ||
+                launch_advance_batch(*P, c->cap_stream) != cudaSuccess)
+                s = fail(&c->err, BUNDLE_ECUDA, "batched step launch failed");
+        }
+    } else {
+        for (size_t k = 0; k < c->members.size() && s == BUNDLE_OK; ++k) {
+            s = launch_iteration(c->members[k], R);
+            if (s != BUNDLE_OK) c->err = "member " + std::to_string(k) + ": " + c->members[k]->err;
+        }
+        if (s == BUNDLE_OK) s = batch_join(c, c->cap_stream);
     }
-    if (s == BUNDLE_OK) s = batch_join(c, c->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     for (size_t k = 0; k < c->members.size(); ++k) c->members[k]->stream = saved[k];

@@ -76,6 +76,16 @@ struct RenderArgs {
     int32_t log_width;
 };
 
+// One launch of the step kernel over many graphs (the batched form): graph m owns the
+// CTAs [blk[m], blk[m + 1]) and its own arguments. Passed by value (kernel parameter
+// space): kBatchLaunch graphs per launch.
+constexpr int kBatchLaunch = 96;
+struct BatchStepArgs {
+    int32_t n;
+    int32_t blk[kBatchLaunch + 1];
+    StepArgs a[kBatchLaunch];
+};
+
 struct FilterArgs {
     const uint32_t* hist;  // [copies][G][H][W]: the histogram is the sum of the copies
     int32_t hist_copies;
@@ -107,6 +117,9 @@ __host__ __device__ inline int64_t quad_elems(int W, int H) {
 
 // Launchers (return the launch status; nothing here synchronises).
 cudaError_t launch_step(int mode, int rho_dtype, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_step_batch(int mode, int rho_dtype, const BatchStepArgs& P, cudaStream_t st);
+// Advance the iteration counter of every graph of P.
+cudaError_t launch_advance_batch(const BatchStepArgs& P, cudaStream_t st);
 cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st);

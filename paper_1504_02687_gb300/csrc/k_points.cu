@@ -132,8 +132,10 @@ __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at
 //     then the arc length by a warp scan and the new point count;
 //  4. offsets of the new polylines (block scan), then one warp per polyline
 //     writes its uniformly re-spaced points and splats them.
+// The work of CTA bx of one graph (a); k_step runs one graph, k_step_batch the CTAs of
+// many graphs in one launch.
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
+__device__ __forceinline__ void step_block(const StepArgs& a, int bx) {
     __shared__ int s_cnt[kEdgesPerBlock];
     __shared__ int s_loc[kEdgesPerBlock + 1];
     __shared__ int s_grp[kEdgesPerBlock];
@@ -147,11 +149,11 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
     __shared__ unsigned char s_pe[kBatchPoints];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t e0 = (int64_t)blockIdx.x * a.eb;
+    const int64_t e0 = (int64_t)bx * a.eb;
     const int nb = (int)min((int64_t)a.eb, a.E - e0);
-    const int64_t region = (int64_t)blockIdx.x * a.eb * a.cap;
+    const int64_t region = (int64_t)bx * a.eb * a.cap;
     const int64_t QC = quad_elems(a.W, a.H);
-    const size_t hist_copy = blockIdx.x % kHistCopies;
+    const size_t hist_copy = bx % kHistCopies;
     const float h = a.h_sched ? __ldg(a.h_sched + __ldg(a.iter)) : a.h;
 
     for (int i = tid; i < nb; i += kStepThreads) {
@@ -338,6 +340,43 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
         }
         b0 = b1;
     }
+}
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kStepThreads) k_step(const __grid_constant__ StepArgs a) {
+    step_block<MODE, T>(a, blockIdx.x);
+}
+
+// Many graphs in one launch: CTA blockIdx.x belongs to graph m with
+// blk[m] <= blockIdx.x < blk[m + 1] and is that graph's CTA blockIdx.x - blk[m].
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kStepThreads, 6) k_step_batch(const __grid_constant__ BatchStepArgs P) {
+    int lo = 0, hi = P.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.blk[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    step_block<MODE, T>(P.a[lo], (int)blockIdx.x - P.blk[lo]);
+}
+
+__global__ void k_advance_batch(const __grid_constant__ BatchStepArgs P) {
+    const int m = threadIdx.x;
+    if (m < P.n) *const_cast<int32_t*>(P.a[m].iter) += 1;
+}
+
+template <typename T>
+cudaError_t launch_step_batch_t(int mode, const BatchStepArgs& P, cudaStream_t st) {
+    const int total = P.blk[P.n];
+    if (total <= 0) return cudaSuccess;
+    switch (mode) {
+        case kModeResample: k_step_batch<kModeResample, T><<<total, kStepThreads, 0, st>>>(P); break;
+        case kModeAdvect: k_step_batch<kModeAdvect, T><<<total, kStepThreads, 0, st>>>(P); break;
+        case kModeAdvectResample:
+            k_step_batch<kModeAdvectResample, T><<<total, kStepThreads, 0, st>>>(P);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -590,6 +629,21 @@ __global__ void k_advance_iter(int32_t* iter) { *iter += 1; }
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_step_batch(int mode, int rho_dtype, const BatchStepArgs& P, cudaStream_t st) {
+    if (P.n < 1 || P.n > kBatchLaunch) return cudaErrorInvalidValue;
+    switch (rho_dtype) {
+        case 0: return launch_step_batch_t<float>(mode, P, st);
+        case 1: return launch_step_batch_t<__nv_bfloat16>(mode, P, st);
+        case 2: return launch_step_batch_t<__half>(mode, P, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_advance_batch(const BatchStepArgs& P, cudaStream_t st) {
+    k_advance_batch<<<1, kBatchLaunch, 0, st>>>(P);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step(int mode, int rho_dtype, const StepArgs& a, cudaStream_t st) {
     switch (rho_dtype) {
