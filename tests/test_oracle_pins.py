@@ -581,6 +581,12 @@ def test_render_width_from_density_and_scale(oracle_mod):
     acc, amb, _ = _render(oracle_mod, seg, rho=rho, width_max=3.0, rho_ref=1 / 0.6)
     assert set(_covered(acc)) == ({(3, x) for x in range(1, 9)} | {(2, x) for x in range(2, 8)}
                                   | {(4, x) for x in range(2, 8)})
+    # log scale: u = 0.5 of the reference gives log2(1.5) = 0.585, width 1 + 2 * 0.585 = 2.17
+    # (radius 1.085): the same 20 pixels as radius 1.1, and none of them near the threshold
+    acc, amb, _ = _render(oracle_mod, seg, rho=rho, width_max=3.0, rho_ref=2.0, log_width=True)
+    assert set(_covered(acc)) == ({(3, x) for x in range(1, 9)} | {(2, x) for x in range(2, 8)}
+                                  | {(4, x) for x in range(2, 8)})
+    assert not amb.any()
     # scale 2: the segment spans image x 5..15 on row 7.0; width 1.5 covers rows 6 and 7
     acc, amb, _ = _render(oracle_mod, seg, scale=2, width_max=1.5, width_min=1.5)
     assert acc.shape == (16, 20, 4)
