@@ -227,7 +227,13 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = make_workload(args.workload, args.edges)
+    if args.workload == "batch":
+        # the batch's sample: its first graph (one graph of the batch is one oracle problem)
+        from paper_1504_02687_gb300 import synth
+
+        w = synth.batch(n_graphs=args.graphs)[0]
+    else:
+        w = make_workload(args.workload, args.edges)
     oracle.build()
     # a bounded sample: 500k edges keep the default 3 + 20 oracle iterations to a few
     # minutes on one core
@@ -256,6 +262,9 @@ def run_reference(args):
     cfg = describe(w, "f64")
     sample = (f"{args.steps} oracle iterations on the first {E} of {w.n_edges} edges of the "
               f"workload, single-threaded FP64")
+    if args.workload == "batch":
+        cfg["workload"] = f"batch of {args.graphs} graphs; the oracle runs its first graph"
+        sample = f"{args.steps} oracle iterations on graph 0 of the batch ({w.name}), FP64"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
