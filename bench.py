@@ -440,6 +440,45 @@ def run_ours(args):
         ps.flags = pkg.FLAG_SEGMENT_HIST
         var["segment_hist"] = {"workload": wc.name, **timed_variant(wc, ps, args.steps),
                                "point_splat": timed_variant(wc, pc, args.steps)}
+        # general interaction matrix (Eq. 3, Sec. 3.2): an ordinal 8 x 8 matrix on the same
+        # workload as the headline, against Eq. 4's mix
+        G = w.n_groups
+        idx = np.arange(G)
+        num = (4 - np.minimum(np.abs(idx[:, None] - idx[None, :]), 5)).astype(np.int64)
+        cm = pkg.bundle_init(params_of(w, args.rho), w.src_xy, w.dst_xy, w.group, w.n_groups,
+                             w.weight, stream=stream)
+        pkg.bundle_set_interaction(cm, num, 4)
+        pkg.bundle_iterate(cm, max(args.warmup, 3))
+        pkg.bundle_sync(cm)
+        d0 = pkg.bundle_get_info(cm).points_processed
+        torch.cuda.synchronize()
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        pkg.bundle_iterate(cm, args.steps)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        mm = ea.elapsed_time(eb)
+        var["interaction_matrix"] = {
+            "value": (pkg.bundle_get_info(cm).points_processed - d0) / (mm / 1e3),
+            "ms_per_step": mm / args.steps, "matrix": f"ordinal {G}x{G}, M(l,b) = (4 - min(|l-b|, 5)) / 4"}
+        pkg.bundle_destroy(cm)
+        # headless drawing (Sec. 3.4) of the 1M-edge workload after 20 iterations, 2x scale
+        cr = pkg.bundle_init(pc, wc.src_xy, wc.dst_xy, wc.group, wc.n_groups, wc.weight,
+                             stream=stream)
+        pkg.bundle_iterate(cr, 20)
+        inf = pkg.bundle_get_info(cr)
+        rgba = torch.empty((inf.grid_h * 2, inf.grid_w * 2, 4), dtype=torch.uint8, device="cuda")
+        pkg.bundle_render(cr, scale=2, alpha=0.05, width_max=4.0, rgba=rgba)  # warm-up
+        torch.cuda.synchronize()
+        t_r = time.perf_counter()
+        pkg.bundle_render(cr, scale=2, alpha=0.05, width_max=4.0, rgba=rgba)
+        t_r = time.perf_counter() - t_r
+        var["render"] = {"workload": wc.name, "image": [inf.grid_w * 2, inf.grid_h * 2],
+                         "ms": t_r * 1e3, "segments": int(inf.n_points - inf.n_edges),
+                         "segments_per_s": (inf.n_points - inf.n_edges) / t_r,
+                         "scope": "bundle_render into a device buffer, wall clock (one call)"}
+        pkg.bundle_destroy(cr)
         # Fig. 3: ink of the segment-rasterised drawing entering each of 10 iterations,
         # optimised vs fixed step, on the 1,000-edge uniform graph
         from paper_1504_02687_gb300 import synth
