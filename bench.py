@@ -156,10 +156,17 @@ def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho):
 
 
 def kernel_source_hash():
+    """Hash of the step kernel's code (its sources without // comments and blank lines: a
+    comment edit does not change the kernel the counters were taken on)."""
+    import re
+
     h = hashlib.sha256()
     for f in ("k_points.cu", "density.cuh", "internal.cuh"):  # the sources of k_step
-        with open(os.path.join(ROOT, "paper_1504_02687_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1504_02687_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

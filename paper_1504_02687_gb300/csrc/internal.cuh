@@ -17,7 +17,7 @@ namespace heb {
 constexpr int kEdgesPerBlock = 128;
 constexpr int kStepThreads = 256;
 constexpr int kBatchPoints = 2048;  // points staged in shared memory per batch
-constexpr int kMaxCap = 64;         // largest polyline (n_fixed or n_max): two warp rounds
+constexpr int kMaxCap = 64;         // largest polyline (n_fixed or n_max): two points per lane
 constexpr float kEdgeGuard = 0.0009765625f;  // positions stay below W - 2^-10
 // The splat writes into kHistCopies copies of the histogram (block b into copy
 // b mod kHistCopies) and the row-pass kernel sums them as it reads: bundled

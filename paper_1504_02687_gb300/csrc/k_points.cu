@@ -128,12 +128,13 @@ __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at
 // batches of whole polylines:
 //  1. load the batch's points (coalesced), map each point to its polyline;
 //  2. advection, one thread per point, in place (a point reads only itself);
-//  3. one warp per polyline: Laplacian smoothing (Jacobi, lanes = points),
-//     then the arc length by a warp scan and the new point count;
-//  4. offsets of the new polylines (block scan), then one warp per polyline
-//     writes its uniformly re-spaced points and splats them.
-// The work of CTA bx of one graph (a); k_step runs one graph, k_step_batch the CTAs of
-// many graphs in one launch.
+//  3. one warp per polyline, two consecutive points per lane: Laplacian
+//     smoothing (Jacobi), then the arc lengths by a warp scan;
+//  4. new point counts (one thread per polyline) and their offsets (block
+//     scan), then one warp per polyline writes its uniformly re-spaced points,
+//     two per lane, and splats them.
+// step_block is the work of CTA bx of one graph (a); k_step runs one graph,
+// k_step_batch the CTAs of many graphs in one launch.
 template <int MODE, typename T>
 __device__ __forceinline__ void step_block(const StepArgs& a, int bx) {
     __shared__ int s_cnt[kEdgesPerBlock];
