@@ -57,6 +57,24 @@ def test_empty_input_is_rejected(pkg):
     assert ei.value.status == pkg.BUNDLE_EINVAL
 
 
+def test_invalid_polylines_are_rejected(pkg):
+    """bundle_init_polylines checks its host inputs before any CUDA call: point counts, the
+    drawing area (a NaN is outside it) and the offsets."""
+    p = pkg.default_params(grid_w=64, grid_h=64, n_fixed=0, n_max=16)
+    off = np.array([0, 3, 5], np.int64)
+    xy = np.array([[1, 1], [5, 5], [9, 2], [3, 3], [7, 7]], np.float32)
+    bad = [
+        (np.array([0, 1, 5], np.int64), xy, "points"),           # a one-point polyline
+        (off, np.where(np.arange(10).reshape(5, 2) == 3, np.nan, xy), "outside"),
+        (off, xy + np.array([64.0, 0.0], np.float32), "outside"),  # beyond W - 2^-10
+        (np.array([1, 3, 5], np.int64), xy, "start at 0"),
+    ]
+    for o, x, needle in bad:
+        with pytest.raises(pkg.BundleError, match=needle) as ei:
+            pkg.bundle_init_polylines(p, o, x)
+        assert ei.value.status == pkg.BUNDLE_EINVAL
+
+
 def test_invalid_groups_and_weights(pkg):
     src, dst = _edges(10)
     p = pkg.default_params(grid_w=64, grid_h=64)
