@@ -347,12 +347,16 @@ bundle_status bundle_profile_read(bundle_ctx* ctx, double* ms, int64_t* launches
  *        half-sample reflection, exactly as BUNDLE_DENSITY_SUMS.
  *  sum_bits must hold 4 (2r+1)^(2(passes-1)) times the histogram's total; the
  *  call does not check this bound (bundle_init does, for its own contexts).
+ *  hist and sums must both live on the current device: the launches and the
+ *  fixed array are those of the current device. The C ABI cannot see their
+ *  sizes; a sums buffer smaller than the stack is written past its end.
  *  stream: cudaStream_t, NULL for the legacy default stream; asynchronous.
  * Returns EINVAL when n_groups * grid_h * grid_w * sum_bits / 8 exceeds
  * 16 MiB or an argument is out of range (message via bundle_last_error(NULL)),
  * ECUDA on a launch failure. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture. All calls share the one array and it keeps the last call's
+ * stream capture. The address is cached per device and CUDA context, so the
+ * first call after a reset of the device looks it up again. All calls share the one array and it keeps the last call's
  * contents; nothing in it needs clearing (the row passes overwrite every cell
  * the column passes read), but calls that overlap on the GPU race on it.
  */

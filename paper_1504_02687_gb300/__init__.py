@@ -403,15 +403,45 @@ def bundle_profile_read(ctx, reset: bool = True) -> dict:
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROFILE_KINDS)}
 
 
+def _noalloc_check(hist, sums):
+    """Reasons the allocation-free call must not be made (the C ABI sees neither sizes,
+    dtypes nor devices, so a mismatch here would become an out-of-bounds write)."""
+    import torch
+
+    if not (isinstance(hist, torch.Tensor) and isinstance(sums, torch.Tensor)):
+        return "hist and sums must be torch tensors"
+    if hist.dim() != 3 or tuple(sums.shape) != tuple(hist.shape):
+        return f"hist and sums must be [G, H, W] of one shape, got {tuple(hist.shape)} and " \
+               f"{tuple(sums.shape)}"
+    if hist.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        return f"hist must be int32 or uint32, got {hist.dtype}"
+    if sums.dtype not in (torch.int32, torch.int64):
+        return f"sums must be int32 or int64, got {sums.dtype}"
+    if not (hist.is_contiguous() and sums.is_contiguous()):
+        return "hist and sums must be contiguous"
+    if not (hist.is_cuda and sums.is_cuda):
+        return "hist and sums must be CUDA tensors"
+    if hist.device != sums.device:
+        return f"hist and sums must be on one device, got {hist.device} and {sums.device}"
+    return None
+
+
 def bundle_smooth_noalloc(hist, sums, radius: int, passes: int, stream=None):
     """Box-pass smoothing of a device histogram into a caller-provided device output, with no
     allocation by the library (for callers that cannot allocate device memory themselves:
-    see include/bundle.h). hist: CUDA uint32/int32 tensor [G, H, W]; sums: CUDA int32 or
-    int64 tensor [G, H, W] (its dtype picks the sum width)."""
+    see include/bundle.h). hist: contiguous CUDA uint32/int32 tensor [G, H, W]; sums:
+    contiguous CUDA int32 or int64 tensor of the same shape on the same device (its dtype
+    picks the sum width). The call runs with that device current."""
+    import torch
+
+    why = _noalloc_check(hist, sums)
+    if why is not None:
+        raise BundleError(BUNDLE_EINVAL, why)
     G, H, W = (int(x) for x in hist.shape)
     bits = 8 * sums.element_size()
-    _check(lib().bundle_smooth_noalloc(_ptr(hist), _ptr(sums), G, H, W, int(radius),
-                                       int(passes), bits, _stream_handle(stream)))
+    with torch.cuda.device(hist.device):
+        _check(lib().bundle_smooth_noalloc(_ptr(hist), _ptr(sums), G, H, W, int(radius),
+                                           int(passes), bits, _stream_handle(stream)))
     return sums
 
 

@@ -23,21 +23,58 @@ constexpr size_t kScratchBytes = size_t(16) << 20;
 __device__ __align__(256) unsigned long long g_smooth_scratch[kScratchBytes / 8];
 
 // In host code the array's name is only a host-side stand-in; the device
-// address comes from cudaGetSymbolAddress, taken once per device with that
-// device current and cached here.
+// address comes from cudaGetSymbolAddress, taken with the device current and
+// cached per device together with the id of the CUDA context it was taken in.
+// A context created after a reset of the device (cudaDeviceReset, or a
+// framework resetting the primary context) has a new id, so the address is
+// looked up again there instead of reusing one that belonged to the old one.
 constexpr int kMaxDevices = 128;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// Id of the calling thread's current context (driver entry points fetched
+// through the runtime, so the library does not link the driver library).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                         cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 cudaError_t scratch_address(int dev, void** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_smooth_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+    unsigned long long id = 0;
+    if (g_scratch_addr[dev] && current_context_id(&id) == cudaSuccess && g_scratch_ctx[dev] == id) {
+        *out = g_scratch_addr[dev];
+        return cudaSuccess;
     }
-    *out = g_scratch_addr[dev];
+    // (the runtime makes the device's context current here if nothing did before)
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_smooth_scratch);
+    if (e != cudaSuccess) return e;
+    if ((e = current_context_id(&id)) != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = id;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -66,6 +103,8 @@ extern "C" bundle_status bundle_smooth_noalloc(const uint32_t* hist, void* sums,
             "fixed intermediate of the allocation-free entry point; use bundle_iterate");
         return BUNDLE_EINVAL;
     }
+    // the launches and the scratch address belong to the current device: hist and sums
+    // must live there
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -74,7 +113,7 @@ extern "C" bundle_status bundle_smooth_noalloc(const uint32_t* hist, void* sums,
     }
     void* Y = nullptr;
     if ((e = scratch_address(dev, &Y)) != cudaSuccess) {
-        heb::set_thread_error("bundle_smooth_noalloc: cudaGetSymbolAddress failed");
+        heb::set_thread_error("bundle_smooth_noalloc: device address of the fixed array not found");
         return BUNDLE_ECUDA;
     }
     heb::FilterArgs f{};

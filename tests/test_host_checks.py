@@ -129,3 +129,23 @@ def test_bounds_of_the_benchmark_configs_fit(pkg):
     assert (4 * 7 + 1) * bound < 2**63
     # the small configuration (2000 edges, 32 points, r = 4, k = 3) fits int32 sums
     assert 4 * 81**2 * 2000 * 32 < 2**31
+
+
+def test_noalloc_binding_rejects_mismatched_buffers(pkg):
+    """The allocation-free smoothing call sees only raw pointers in the C ABI, so its
+    binding refuses shapes, dtypes, layouts and devices that would let the kernels write
+    past the caller's output, before anything reaches the library (CPU tensors here)."""
+    torch = pytest.importorskip("torch")
+    h = torch.zeros((2, 16, 16), dtype=torch.int32)
+    cases = [
+        (h, torch.zeros((2, 16, 8), dtype=torch.int64), "one shape"),
+        (h.view(2, 256), torch.zeros((2, 256), dtype=torch.int64), "one shape"),
+        (h, torch.zeros((2, 16, 16), dtype=torch.float32), "int32 or int64"),
+        (h.to(torch.float32), torch.zeros((2, 16, 16), dtype=torch.int64), "int32 or uint32"),
+        (h, torch.zeros((2, 16, 32), dtype=torch.int64)[:, :, ::2], "contiguous"),
+        (h, torch.zeros((2, 16, 16), dtype=torch.int64), "CUDA tensors"),
+    ]
+    for hist, sums, needle in cases:
+        with pytest.raises(pkg.BundleError, match=needle) as ei:
+            pkg.bundle_smooth_noalloc(hist, sums, 2, 2)
+        assert ei.value.status == pkg.BUNDLE_EINVAL
