@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="one graph's edges split over the ranks, histograms all-reduced each "
+                         "iteration (strong scaling); default: an independent graph per rank")
     return ap.parse_args()
 
 
@@ -132,8 +135,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho):
-    """Bytes one launch of each kernel must move (its roofline numerator).
+def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho, MC=None):
+    """Bytes one launch of each kernel must move (its roofline numerator). GC: histogram
+    cells (groups x H x W); MC: entries of the padded density map (groups x (H+4) x (W+4)).
 
     advect+resample: read and write every point (8 B each way), per-edge count in and out,
     group and weight (16 B), one read of the density stack, the histogram written once.
@@ -148,10 +152,9 @@ def algorithmic_bytes(kind, N, E, GC, b_sum, b_rho):
         return GC * (4 + b_sum)  # the histogram once (its copies are workspace) + the output
     if kind == "colbox":
         return 2 * GC * b_sum
-    if kind == "combine":
-        return GC * (b_sum + b_rho)
-    if kind == "quads":
-        return GC * b_rho * 5
+    if kind == "mix_quads":
+        # the sums once, the density quad map (four densities per quad) written once
+        return GC * b_sum + 4 * (GC if MC is None else MC) * b_rho
     return 0
 
 
@@ -200,8 +203,6 @@ def peaks():
 def cpu_baseline(w, sample_edges, iters=1):
     """The FP64 oracle as it stands, single-threaded, `iters` iterations on the first
     `sample_edges` edges of the same graph (same grid, groups, filter)."""
-    import numpy as np
-
     import oracle
 
     oracle.build()
@@ -219,10 +220,91 @@ def cpu_baseline(w, sample_edges, iters=1):
         off, xy = res.off, res.xy
         n += int(res.off[-1])  # points advected by this iteration
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": (f"{iters} iteration(s) of the FP64 oracle from straight edges on the first "
                        f"{E} of {w.n_edges} edges ({n} sample-point updates, full "
-                       f"{w.n_groups}x{H_}x{W_} grid), {dt:.1f} s")}
+                       f"{w.n_groups}x{H_}x{W_} grid), {dt:.1f} s, single-threaded")}
+
+
+def _oracle_job(job):
+    """One FP64 oracle run in a worker process (spawned: no CUDA state is inherited)."""
+    import oracle
+
+    off, xy, group, weight, G, H, W, prm, iters = job
+    r = oracle.run(off, xy, group, weight, G, H, W, oracle.Params(**prm), 0, iters)
+    return r.off, r.xy
+
+
+def precision_forms(w, pkg, stream, sample_edges=200_000, iters=30):
+    """Precision form on a bounded sample of the workload (its first `sample_edges` edges on
+    the full grid with the full workload's groups and filter): the GPU run with the density
+    stack stored in FP32, BF16 and FP16 (histograms and sums integer, positions and gradients
+    FP32) against the FP64 oracle from the same FP32 start after `iters` iterations. Errors
+    are in units of the layout extent, measured on the polylines re-spaced to 9 points
+    (resampled counts can differ after a near-tie), beside the FP64 method's own drift when
+    its start moves by +-1 FP32 ulp (two seeds). The oracle runs in spawned worker
+    processes after every GPU measurement of the line is done."""
+    import multiprocessing as mp_
+
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    E = min(sample_edges, w.n_edges)
+    W_, H_ = w.grid
+    g = w.group[:E]
+    wt = None if w.weight is None else w.weight[:E]
+    out = {"sample": f"first {E} of {w.n_edges} edges, {w.n_groups}x{H_}x{W_} grid, "
+                     f"{iters} iterations", "forms": {}}
+    start = None
+    got = {}
+    for name in ("f32", "bf16", "f16"):
+        prm = params_of(w, name)
+        ctx = pkg.bundle_init(prm, w.src_xy[:E], w.dst_xy[:E], g, w.n_groups, wt, stream=stream)
+        try:
+            off0, P0 = pkg.bundle_fetch(ctx, pixels=True)
+            if start is None:
+                start = (off0.astype(np.int64), P0.astype(np.float64), prm)
+            pkg.bundle_iterate(ctx, iters)
+            o, x = pkg.bundle_fetch(ctx, pixels=True)
+            got[name] = (o.astype(np.int64), x.astype(np.float64))
+        finally:
+            pkg.bundle_destroy(ctx)
+    off0, P0, prm = start
+    op = dict(radius=prm.radius, passes=prm.passes, alpha_num=prm.alpha_num,
+              alpha_den=prm.alpha_den, h_max_sigmas=prm.h_max_sigmas, lam=prm.lambda_,
+              n_fixed=prm.n_fixed, n_max=prm.n_max, delta=float(prm.delta_px),
+              beta=float(prm.laplace_beta), eps=float(prm.eps), tries=prm.step_tries)
+
+    def perturbed(seed):
+        rng = np.random.default_rng(seed)
+        x32 = P0.astype(np.float32)
+        d = rng.integers(-1, 2, x32.shape)
+        up, dn = np.nextafter(x32, np.float32(1e9)), np.nextafter(x32, np.float32(-1e9))
+        return np.where(d > 0, up, np.where(d < 0, dn, x32)).astype(np.float64)
+
+    jobs = [(off0, xy, g, wt, w.n_groups, H_, W_, op, iters)
+            for xy in (P0, perturbed(0), perturbed(1))]
+    t0 = time.perf_counter()
+    with mp_.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_job, jobs)
+    out["oracle_seconds_wall"] = time.perf_counter() - t0
+    ref_off, ref_xy = res[0]
+    extent = float(max(W_, H_))
+    o2, r2 = oracle.resample(ref_off, ref_xy, 9, 64, 2.0)
+
+    def err(off, xy):
+        o1, r1 = oracle.resample(off, xy, 9, 64, 2.0)
+        e = np.hypot(*(r1 - r2).T) / extent
+        return {"max": float(e.max()), "rms": float(np.sqrt((e ** 2).mean()))}
+
+    for name, (o, x) in got.items():
+        out["forms"][name] = {**err(o, x), "same_counts": bool(np.array_equal(o, ref_off))}
+    out["fp64_ulp_envelope"] = [err(o, x) for o, x in res[1:]]
+    out["units"] = "fraction of the layout extent (max(W, H) px)"
+    return out
 
 
 def run_reference(args):
@@ -267,6 +349,11 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = pts / dt
     cfg = describe(w, "f64")
+    if E < w.n_edges:
+        # the line names what the oracle times: the first E edges of the workload's graph
+        cfg["workload"] = (f"{E}-edge sample (the first {E} of {w.n_edges} edges) of "
+                           + cfg["workload"])
+        cfg["sample_edges"] = E
     sample = (f"{args.steps} oracle iterations on the first {E} of {w.n_edges} edges of the "
               f"workload, single-threaded FP64")
     if args.workload == "batch":
@@ -277,8 +364,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -331,6 +418,7 @@ def run_ours(args):
     ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight, stream=stream)
     info = pkg.bundle_get_info(ctx)
     GC = info.n_groups * info.grid_w * info.grid_h
+    MC = info.n_groups * (info.grid_w + 3) * (info.grid_h + 3)
     b_sum = info.sum_bits // 8
     b_rho = 4 if args.rho == "f32" else 2
 
@@ -378,21 +466,20 @@ def run_ours(args):
     launches = sum(n for k, (t, n) in kern.items() if k != "hist_clear") + args.steps + 1
     dom = max((k for k in kern if k != "hist_clear"), key=lambda k: kern[k][0])
     dom_ms = kern[dom][0] / kern[dom][1]
-    dom_bytes = algorithmic_bytes(dom, N_prof, E, GC, b_sum, b_rho)
+    dom_bytes = algorithmic_bytes(dom, N_prof, E, GC, b_sum, b_rho, MC)
     peak, peak_src = peaks()
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     traffic = measured_traffic(dom, w.name, dom_bytes)
     per_kernel = {}
     for k, (tms, n) in kern.items():
-        b = algorithmic_bytes(k, N_prof, E, GC, b_sum, b_rho)
+        b = algorithmic_bytes(k, N_prof, E, GC, b_sum, b_rho, MC)
         per_kernel[k] = {"launches": n, "ms_per_launch": tms / n,
                          "share": tms / max(sum(v[0] for v in kern.values()), 1e-9),
                          "algorithmic_gbs": (b / (tms / n / 1e3) / 1e9) if b else None}
     step_bytes = (algorithmic_bytes("advect_resample", N_avg, E, GC, b_sum, b_rho)
                   + algorithmic_bytes("rowbox", N_avg, E, GC, b_sum, b_rho)
                   + algorithmic_bytes("colbox", N_avg, E, GC, b_sum, b_rho)
-                  + algorithmic_bytes("combine", N_avg, E, GC, b_sum, b_rho)
-                  + algorithmic_bytes("quads", N_avg, E, GC, b_sum, b_rho))
+                  + algorithmic_bytes("mix_quads", N_avg, E, GC, b_sum, b_rho, MC))
     pkg.bundle_destroy(ctx)
 
     out = {
@@ -433,7 +520,8 @@ def run_ours(args):
             pkg.bundle_destroy(c2)
             return {"value": u2 / (m2 / 1e3), "ms_per_step": m2 / steps}
 
-        var = {"bf16": timed_variant(w, params_of(w, "bf16"), args.steps)}
+        var = {"bf16": timed_variant(w, params_of(w, "bf16"), args.steps),
+               "fp16": timed_variant(w, params_of(w, "f16"), args.steps)}
         # KDEEB's fixed step (Sec. 3.3) on the same workload: the cost of the density test
         pf = params_of(w, args.rho)
         pf.flags = pkg.FLAG_FIXED_STEP
@@ -502,6 +590,10 @@ def run_ours(args):
             conv[name] = pkg.bundle_fetch_ink(c4, 0, 10)[:, 0].tolist()
             pkg.bundle_destroy(c4)
         var["convergence"] = conv
+        # the batched form (64 graphs, one graph launch per iteration, autotuned tiles)
+        # against the same graphs bundled one after another
+        var["batch"] = measure_batch(pkg, torch, stream, args.graphs, min(args.steps, 10),
+                                     max(args.warmup, 3), args.rho)
         out["variants"] = var
 
     if not args.no_e2e:
@@ -538,98 +630,191 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         # about 10-20 s of single-core oracle work: 2 iterations over the whole graph
         out["cpu_baseline"] = cpu_baseline(w, w.n_edges, iters=2 if args.workload != "small" else 10)
+        if not args.no_variants and args.workload == "lattice" and args.rho == "f32":
+            # the oracle's 30-iteration positions on a bounded sample against the GPU's
+            # precision forms (after every timed measurement above)
+            out.setdefault("variants", {})["precision"] = precision_forms(w, pkg, stream)
     if rank == 0:
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
 
 
-def run_batch(args):
+def measure_batch(pkg, torch, stream, n_graphs, steps, warmup, rho):
     """Batched form: many independent graphs per iteration (one CUDA graph launch runs an
-    iteration of all of them), against the same graphs bundled one after another."""
-    import torch
+    iteration of all of them, tiles chosen by the autotuner), against the same batch with the
+    size-rule tiles and against the same graphs bundled one after another."""
+    from paper_1504_02687_gb300 import synth
 
-    import paper_1504_02687_gb300 as pkg
-    from paper_1504_02687_gb300 import build as lib_build, synth
-
-    torch.cuda.set_device(0)
-    lib_build.build()
-    ws = synth.batch(n_graphs=args.graphs)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    ps = [params_of(w, args.rho) for w in ws]
+    ws = synth.batch(n_graphs=n_graphs)
+    ps = [params_of(w, rho) for w in ws]
     descs = [dict(src_xy=w.src_xy, dst_xy=w.dst_xy, group=w.group, n_groups=w.n_groups,
                   weight=w.weight) for w in ws]
-    clocks = ClockSampler(torch.cuda.current_device())
-    b = pkg.bundle_init_batch(descs, ps, stream=stream)
-    # tile shapes measured per graph on its own edges (same results whatever they are)
-    t_tune = time.perf_counter()
-    pkg.bundle_autotune(b)
-    t_tune = time.perf_counter() - t_tune
-    tiles = {}
-    for k in range(pkg.bundle_batch_size(b)):
-        inf = pkg.bundle_get_info(pkg.bundle_batch_member(b, k))
-        key = f"eb{inf.tile_eb}/row{inf.tile_row}/strip{inf.tile_strip}"
-        tiles[key] = tiles.get(key, 0) + 1
-    pkg.bundle_iterate(b, args.warmup)
-    pkg.bundle_sync(b)
-    d0 = pkg.bundle_get_info(b).points_processed
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    pkg.bundle_iterate(b, args.steps)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    upd = pkg.bundle_get_info(b).points_processed - d0
-    pkg.bundle_destroy(b)
-    # the same batch with the size-heuristic tiles
-    b = pkg.bundle_init_batch(descs, ps, stream=stream)
-    pkg.bundle_iterate(b, args.warmup)
-    pkg.bundle_sync(b)
-    h0 = pkg.bundle_get_info(b).points_processed
-    torch.cuda.synchronize()
-    t0.record(stream)
-    pkg.bundle_iterate(b, args.steps)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    heur_ms = t0.elapsed_time(t1)
-    heur_upd = pkg.bundle_get_info(b).points_processed - h0
-    pkg.bundle_destroy(b)
-    # the same graphs, one plain context at a time
+
+    def timed_batch(tune):
+        b = pkg.bundle_init_batch(descs, ps, stream=stream)
+        t_tune, tiles = 0.0, {}
+        if tune:
+            t_tune = time.perf_counter()
+            pkg.bundle_autotune(b)
+            t_tune = time.perf_counter() - t_tune
+            for k in range(pkg.bundle_batch_size(b)):
+                inf = pkg.bundle_get_info(pkg.bundle_batch_member(b, k))
+                key = f"eb{inf.tile_eb}/row{inf.tile_row}/strip{inf.tile_strip}"
+                tiles[key] = tiles.get(key, 0) + 1
+        pkg.bundle_iterate(b, warmup)
+        pkg.bundle_sync(b)
+        d0 = pkg.bundle_get_info(b).points_processed
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        pkg.bundle_iterate(b, steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        upd = pkg.bundle_get_info(b).points_processed - d0
+        pkg.bundle_destroy(b)
+        return ms, upd, t_tune, tiles
+
+    ms, upd, t_tune, tiles = timed_batch(True)
+    heur_ms, heur_upd, _, _ = timed_batch(False)
     seq_ms, seq_upd = 0.0, 0
     for w, p in zip(ws, ps):
         c = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight, stream=stream)
-        pkg.bundle_iterate(c, args.warmup)
+        pkg.bundle_iterate(c, warmup)
         pkg.bundle_sync(c)
         e0 = pkg.bundle_get_info(c).points_processed
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        pkg.bundle_iterate(c, args.steps)
+        pkg.bundle_iterate(c, steps)
         a1.record(stream)
         torch.cuda.synchronize()
         seq_ms += a0.elapsed_time(a1)
         seq_upd += pkg.bundle_get_info(c).points_processed - e0
         pkg.bundle_destroy(c)
-    clk = clocks.stop()
     E = sum(w.n_edges for w in ws)
-    print(json.dumps({
-        "metric": METRIC, "value": upd / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded clustered graphs)",
-        "config": {"workload": (f"batch of {len(ws)} graphs, {E} edges in total (log-uniform "
-                                "10k-500k), 1-16 groups, grids 256^2/512^2/1024^2, r 4-12, "
-                                "k=3, <= 64 samples/edge"), "graphs": len(ws), "edges": E,
-                   "points_per_step": upd / args.steps, "rho_dtype": args.rho},
+    return {
+        "workload": (f"batch of {len(ws)} graphs, {E} edges in total (log-uniform 10k-500k), "
+                     "1-16 groups, grids 256^2/512^2/1024^2, r 4-12, k=3, <= 64 samples/edge"),
+        "graphs": len(ws), "edges": E, "steps": steps, "rho_dtype": rho,
+        "value": upd / (ms / 1e3), "ms_per_step": ms / steps, "points_per_step": upd / steps,
         "autotune": {"seconds": t_tune, "tiles": tiles,
                      "untuned_batch": {"value": heur_upd / (heur_ms / 1e3),
-                                       "ms_per_step": heur_ms / args.steps}},
-        "sequential": {"value": seq_upd / (seq_ms / 1e3), "ms_per_step": seq_ms / args.steps,
-                       "speedup_of_batch": (upd / ms) / (seq_upd / seq_ms)},
+                                       "ms_per_step": heur_ms / steps}},
+        "sequential": {"value": seq_upd / (seq_ms / 1e3), "ms_per_step": seq_ms / steps},
+        "speedup_over_sequential": (upd / ms) / (seq_upd / seq_ms),
+    }
+
+
+def run_split(args):
+    """One graph split over the ranks (SURVEY's multi-GPU form, Sec. 4's edges over threads):
+    rank r bundles edges [r E / N, (r + 1) E / N) and the splatted histograms are summed over
+    the ranks each iteration (NCCL all-reduce of the int32 stack), so every rank advects on
+    the whole graph's density. Strong scaling: the whole job is one graph."""
+    import numpy as np
+    import torch
+
+    import paper_1504_02687_gb300 as pkg
+    from paper_1504_02687_gb300 import build as lib_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        lib_build.build()
+    if dist:
+        dist.barrier()
+    lib_build.build()
+    w = make_workload(args.workload, args.edges)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    p = params_of(w, args.rho)
+    # the whole graph's grid map, pixel-unit straight edges and integer widths (a context over
+    # all edges, destroyed before any iteration)
+    full = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight, stream=stream)
+    off0, xy0 = pkg.bundle_fetch(full, pixels=True)
+    finfo = pkg.bundle_get_info(full)
+    map5 = np.array(finfo.map)
+    pkg.bundle_destroy(full)
+    E = w.n_edges
+    lo, hi = rank * E // world, (rank + 1) * E // world
+    pp = params_of(w, args.rho)
+    pp.sum_bits = finfo.sum_bits
+    ctx = pkg.bundle_init_polylines(pp, off0[lo:hi + 1] - off0[lo], xy0[off0[lo]:off0[hi]],
+                                    w.group[lo:hi], w.n_groups,
+                                    None if w.weight is None else w.weight[lo:hi], map5=map5,
+                                    stream=stream)
+    reduce = (lambda t: dist.all_reduce(t)) if dist else (lambda t: None)
+    clocks = ClockSampler(torch.cuda.current_device())
+    pkg.bundle_iterate_split(ctx, args.warmup, reduce, on_device=True)
+    pkg.bundle_sync(ctx)
+    done0 = pkg.bundle_get_info(ctx).points_processed
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    pkg.bundle_iterate_split(ctx, args.steps, reduce, on_device=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    updates = pkg.bundle_get_info(ctx).points_processed - done0
+    clk = clocks.stop()
+    pkg.bundle_destroy(ctx)
+    ms, total = reduce_over_ranks(dist, ms, float(updates), device="cuda")
+    if rank == 0:
+        cfg = describe(w, args.rho)
+        cfg["parallelism"] = (f"{world}-way edge split of one graph, int32 histogram all-reduce "
+                              "per iteration" if world > 1 else
+                              "one graph through the split-form entry points, no exchange")
+        cfg["points_per_step"] = total / args.steps
+        print(json.dumps({
+            "metric": METRIC, "value": total / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator shaped like the paper's graphs)", "config": cfg,
+            "clocks": clk}))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_batch(args):
+    """The batched form as the timed workload (`--workload batch`)."""
+    import torch
+
+    import paper_1504_02687_gb300 as pkg
+    from paper_1504_02687_gb300 import build as lib_build
+
+    torch.cuda.set_device(0)
+    lib_build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    clocks = ClockSampler(torch.cuda.current_device())
+    r = measure_batch(pkg, torch, stream, args.graphs, args.steps, args.warmup, args.rho)
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded clustered graphs)",
+        "config": {"workload": r["workload"], "graphs": r["graphs"], "edges": r["edges"],
+                   "points_per_step": r["points_per_step"], "rho_dtype": args.rho},
+        "autotune": r["autotune"],
+        "sequential": {**r["sequential"], "speedup_of_batch": r["speedup_over_sequential"]},
         "clocks": clk,
     }))
 
@@ -640,6 +825,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.split:
+        run_split(args)
     else:
         run_ours(args)
 

@@ -291,8 +291,8 @@ bundle_status bundle_render(bundle_ctx* ctx, const bundle_render_params* params,
 /*
  * Autotuner for the tile shapes (the paper has no counterpart; its CPU threads need
  * none). On a context fresh from bundle_init (or a batch of them, each graph tuned on
- * its own edges), times on the GPU: the edges per block of the point kernels (16, 32,
- * 64, 128; each candidate resamples, splats and filters the straight edges, then
+ * its own edges), times on the GPU: the edges per block of the point kernels (4, 8,
+ * 16, 32 -- one warp works through each block; each candidate resamples, splats and filters the straight edges, then
  * the fused advect + resample step is timed), the row-pass variant and the column-pass
  * strip, and keeps the fastest of each (bundle_info.tile_*). Results do not depend on
  * the tiles: every choice gives the same bits. The context returns to its fresh state
@@ -302,7 +302,8 @@ bundle_status bundle_render(bundle_ctx* ctx, const bundle_render_params* params,
 bundle_status bundle_autotune(bundle_ctx* ctx);
 
 /* Set the tiles by hand (e.g. those an earlier bundle_autotune chose for the same
- * shape): eb 0 (keep) or 16, 32, 64, 128 -- only on a fresh bundle_init context;
+ * shape): eb 0 (keep) or 4, 8, 16, 32 edges per warp-owned block of the point
+ * layout -- only on a fresh bundle_init context;
  * row_mode 0 (by width), 1 (register rows, widths of 225..256, 481..512 or 993..1024
  * cells), 2 (shared-memory rows); col_strip 0 (by height), 2, 4 or 8 (when the strip's
  * column fits in shared memory). EINVAL for a choice that does not exist, ESTATE for
@@ -318,9 +319,9 @@ bundle_status bundle_get_info(const bundle_ctx* ctx, bundle_info* out);
  * every launch of bundle_iterate (a tracing aid; off by default, adds two event
  * records per launch). Kinds, in order: 0 resample+splat, 1 advect+Laplacian,
  * 2 advect+Laplacian+resample+splat, 3 row box passes, 4 column box passes,
- * 5 layer mix, 6 histogram clear, 7 density quad build.
+ * 5 layer mix into the density quad map, 6 histogram clear.
  */
-#define BUNDLE_PROFILE_KINDS 8
+#define BUNDLE_PROFILE_KINDS 7
 bundle_status bundle_profile_enable(bundle_ctx* ctx, int32_t on);
 
 /*
@@ -363,6 +364,35 @@ bundle_status bundle_profile_read(bundle_ctx* ctx, double* ms, int64_t* launches
 bundle_status bundle_smooth_noalloc(const uint32_t* hist, void* sums, int32_t n_groups,
                                     int32_t grid_h, int32_t grid_w, int32_t radius,
                                     int32_t passes, int32_t sum_bits, void* stream);
+
+/*
+ * Split form: one graph's edges divided over several contexts -- one per process or
+ * GPU -- that together give exactly the run of one context over all edges (Sec. 4
+ * divides a graph's edges over CPU threads the same way). Every per-edge stage runs
+ * on a context's own edges; the histogram, the only state that couples edges, is
+ * summed over the contexts between the splat and the box passes (an integer sum:
+ * exact and order-free, e.g. an all-reduce). The contexts must share the grid map:
+ * create them with bundle_init_polylines from pixel-unit polylines and one map, and
+ * set params.sum_bits to the width the whole graph needs (a context sizes its
+ * integers for its own edges otherwise, too small for the summed histogram).
+ * A run of n iterations on each context:
+ *   bundle_points_step(ctx, 0)                     resample + splat (opens the run)
+ *   repeat n times:
+ *     fetch BUNDLE_DENSITY_HIST, sum it over the contexts, bundle_set_histogram
+ *     bundle_density_step(ctx)                     box passes, layer mix, density
+ *     bundle_points_step(ctx, last ? BUNDLE_STEP_LAST : 0)
+ *                                                  advect + Laplacian (+ resample +
+ *                                                  splat for the next iteration)
+ * With one context and no exchange this is bundle_iterate(ctx, n), bit for bit.
+ * ESTATE when a call comes out of this order; bundle_iterate refuses while a run is
+ * open. Asynchronous on the context's stream (host-memory histograms synchronise).
+ */
+#define BUNDLE_STEP_LAST 1 /* bundle_points_step: the last iteration of the run */
+bundle_status bundle_points_step(bundle_ctx* ctx, int32_t flags);
+bundle_status bundle_density_step(bundle_ctx* ctx);
+/* Replace the splatted histogram of the open iteration by src (uint32 [G][H][W],
+ * flags BUNDLE_INPUT_DEVICE for a device pointer), e.g. its sum over the contexts. */
+bundle_status bundle_set_histogram(bundle_ctx* ctx, const uint32_t* src, int32_t flags);
 
 /* Wait for the context's stream; reports a deferred kernel error as ECUDA. */
 bundle_status bundle_sync(bundle_ctx* ctx);

@@ -29,9 +29,10 @@ FLAG_SEGMENT_HIST = 2
 FLAG_INK_STATS = 4
 INK_STATS_CAP = 4096
 FETCH_DEVICE, FETCH_PIXELS, FETCH_RESAMPLED = 1, 2, 4
+STEP_LAST = 1
 DENSITY_HIST, DENSITY_SUMS, DENSITY_RHO = 0, 1, 2
-PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "combine",
-                 "hist_clear", "quads")
+PROFILE_KINDS = ("resample", "advect", "advect_resample", "rowbox", "colbox", "mix_quads",
+                 "hist_clear")
 
 EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bundle_iterate",
             "bundle_fetch", "bundle_fetch_density", "bundle_get_info", "bundle_sync",
@@ -39,7 +40,8 @@ EXPORTED = ("bundle_default_params", "bundle_init", "bundle_init_polylines", "bu
             "bundle_profile_enable", "bundle_profile_read", "bundle_smooth_noalloc",
             "bundle_init_batch", "bundle_batch_size", "bundle_batch_member",
             "bundle_set_interaction", "bundle_fetch_ink", "bundle_render", "bundle_autotune",
-            "bundle_set_tiles")
+            "bundle_set_tiles", "bundle_points_step", "bundle_density_step",
+            "bundle_set_histogram")
 
 
 class BundleParams(ctypes.Structure):
@@ -155,6 +157,12 @@ def lib():
     L.bundle_fetch_ink.argtypes = [P, P, i32, i32]
     L.bundle_fetch_ink.restype = i32
     L.bundle_set_interaction.restype = i32
+    L.bundle_points_step.argtypes = [P, i32]
+    L.bundle_points_step.restype = i32
+    L.bundle_density_step.argtypes = [P]
+    L.bundle_density_step.restype = i32
+    L.bundle_set_histogram.argtypes = [P, P, i32]
+    L.bundle_set_histogram.restype = i32
     _lib = L
     return L
 
@@ -306,6 +314,49 @@ def bundle_set_tiles(ctx, eb: int = 0, row_mode: int = 0, col_strip: int = 0):
 
 def bundle_iterate(ctx, n_iters: int):
     _check(lib().bundle_iterate(ctx, int(n_iters)), ctx)
+
+
+def bundle_points_step(ctx, last: bool = False):
+    """Split form: the per-edge stages of an iteration on this context's edges (see
+    include/bundle.h): the first call of a run resamples and splats; later calls advect,
+    smooth, and (unless `last`) resample and splat for the next iteration."""
+    _check(lib().bundle_points_step(ctx, STEP_LAST if last else 0), ctx)
+
+
+def bundle_density_step(ctx):
+    """Split form: box passes, layer mix and density of the open iteration's histogram."""
+    _check(lib().bundle_density_step(ctx), ctx)
+
+
+def bundle_set_histogram(ctx, hist):
+    """Split form: replace the open iteration's histogram (uint32/int32 [G, H, W]; numpy, or
+    a CUDA tensor on the context's device), e.g. by its sum over the contexts."""
+    if _is_device(hist):
+        if not hist.is_contiguous():
+            raise BundleError(BUNDLE_EINVAL, "hist must be contiguous")
+        _check(lib().bundle_set_histogram(ctx, _ptr(hist), INPUT_DEVICE), ctx)
+    else:
+        h = np.ascontiguousarray(hist).view(np.uint32)
+        _check(lib().bundle_set_histogram(ctx, _ptr(h), 0), ctx)
+
+
+def bundle_iterate_split(ctx, n_iters: int, all_reduce, on_device: bool = True):
+    """n iterations of a context that holds part of a graph's edges. `all_reduce(h)` must sum
+    the int32 [G, H, W] tensor h over all parts in place (e.g. torch.distributed.all_reduce:
+    on_device=True hands it a CUDA tensor, for NCCL; False a CPU tensor, for gloo). The
+    integer sum is exact, so every part sees the histogram of the whole graph."""
+    import torch
+
+    info = bundle_get_info(ctx)
+    shape = (info.n_groups, info.grid_h, info.grid_w)
+    buf = torch.empty(shape, dtype=torch.int32, device="cuda" if on_device else "cpu")
+    bundle_points_step(ctx)
+    for it in range(int(n_iters)):
+        bundle_fetch_density(ctx, DENSITY_HIST, out=buf if on_device else buf.numpy())
+        all_reduce(buf)
+        bundle_set_histogram(ctx, buf if on_device else buf.numpy())
+        bundle_density_step(ctx)
+        bundle_points_step(ctx, last=it == n_iters - 1)
 
 
 def bundle_sync(ctx):

@@ -24,7 +24,7 @@ struct bundle_ctx {
     int64_t E = 0;
     int32_t G = 1, W = 0, H = 0;
     int32_t cap = 0;
-    int32_t eb = kEdgesPerBlock;  // edges per block of the point layout
+    int32_t eb = kMaxEdgesPerWarp;  // edges per block of the point layout (one warp each)
     int64_t n_blocks = 0;
     int32_t col_strip = 0;        // column-pass strip (0: by height), set by the autotuner
     int32_t row_mode = 0;         // row-pass variant (0: by width), set by the autotuner
@@ -53,7 +53,7 @@ struct bundle_ctx {
     void* Y = nullptr;
     void* S = nullptr;
     void* rho = nullptr;
-    void* quads = nullptr;
+    void* quads = nullptr;   // [G][H+3][W+3] density quads
     unsigned long long* counters = nullptr;  // [0] points splatted, [1] scratch sum, [2] segment mass
     int64_t* fetch_off = nullptr;
     int64_t* fetch_tmp = nullptr;
@@ -61,6 +61,11 @@ struct bundle_ctx {
     int64_t fetch_xy_cap = 0;
     int cur_P = 0;       // buffer holding the current polylines
     int cur_R = -1;      // buffer holding the last resampled polylines (-1: none yet)
+    // split form (bundle_points_step / bundle_density_step): 0 no run open, 1 histogram of
+    // the open iteration splatted (it may be replaced before the density stage), 2 density
+    // of the open iteration built; split_R: buffer of the resampled polylines of the run
+    int split_state = 0;
+    int split_R = 0;
     bool have_density = false;
     int64_t device_bytes = 0;
     // device schedule of h and the graphs of one steady-state iteration (one per ping-pong
@@ -359,10 +364,10 @@ bundle_status grid_map(bundle_ctx* c, const float* src, const float* dst, std::s
 // Device buffers sized from E, cap, G, H, W and the widths.
 bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     const int64_t E = c->E;
-    // blocks of up to 128 edges; small graphs use smaller blocks so that at least ~4 CTAs
-    // per SM (152 SMs) have work
-    int eb = kEdgesPerBlock;
-    while (eb > 8 && E < (int64_t)eb * 152 * 4) eb /= 2;
+    // blocks of up to 32 edges, one warp each; small graphs use smaller blocks so that at
+    // least ~16 warps per SM (152 SMs) have work
+    int eb = kMaxEdgesPerWarp;
+    while (eb > 4 && E < (int64_t)eb * 152 * 16) eb /= 2;
     c->eb = eb;
     c->n_blocks = (E + eb - 1) / eb;
     // sized for blocks of kEdgesPerBlock whatever eb is, so that the autotuner can move the
@@ -494,7 +499,7 @@ bool to_host(const T* p, int64_t n, bool on_device, std::vector<T>* v, const T**
 }
 
 enum ProfileKind { kProfResample = 0, kProfAdvect, kProfAdvectResample, kProfRowbox,
-                   kProfColbox, kProfCombine, kProfHistClear, kProfQuads, kProfKinds };
+                   kProfColbox, kProfMixQuads, kProfHistClear, kProfKinds };
 
 // Launch through `fn`, bracketed by two events when profiling is on.
 template <typename F>
@@ -573,7 +578,8 @@ bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
     return BUNDLE_OK;
 }
 
-bundle_status run_filter(bundle_ctx* c) {
+// Arguments of the grid-side kernels of context c.
+FilterArgs filter_args(bundle_ctx* c) {
     FilterArgs f{};
     f.hist = c->hist;
     f.hist_copies = kHistCopies;
@@ -592,15 +598,19 @@ bundle_status run_filter(bundle_ctx* c) {
     f.den_f = c->den_f;
     f.strip = c->col_strip;
     f.row_mode = c->row_mode;
+    return f;
+}
+
+bundle_status run_filter(bundle_ctx* c) {
+    const FilterArgs f = filter_args(c);
     if (c->ink)
         CUDA_TRY(&c->err, launch_ink(c->hist, (int64_t)c->H * c->W, c->G, kHistCopies, c->ink,
                                      c->d_iter, BUNDLE_INK_STATS_CAP, c->n_sm, c->stream));
     CUDA_TRY(&c->err, timed(c, kProfRowbox, [&] { return launch_rowbox(c->sum_bits, f, c->stream); }));
     CUDA_TRY(&c->err, timed(c, kProfColbox, [&] { return launch_colbox(c->sum_bits, f, c->stream); }));
-    CUDA_TRY(&c->err, timed(c, kProfCombine, [&] {
-                 return launch_combine(c->sum_bits, c->p.rho_dtype, f, c->stream);
+    CUDA_TRY(&c->err, timed(c, kProfMixQuads, [&] {
+                 return launch_mix_quads(c->sum_bits, c->p.rho_dtype, f, c->stream);
              }));
-    CUDA_TRY(&c->err, timed(c, kProfQuads, [&] { return launch_quads(c->p.rho_dtype, f, c->stream); }));
     return BUNDLE_OK;
 }
 
@@ -639,7 +649,7 @@ bundle_status ensure_schedule(bundle_ctx* c, int32_t needed) {
     return BUNDLE_OK;
 }
 
-// One steady-state iteration: layer filter, mix, quads, histogram clear, the fused
+// One steady-state iteration: layer filter, mix into the density quads, histogram clear, the fused
 // advect -> resample -> splat step from buffer R to 1 - R, then the counter advance.
 bundle_status launch_iteration(bundle_ctx* c, int R) {
     bundle_status s = run_filter(c);
@@ -984,7 +994,7 @@ static bundle_status build_batch_graph(bundle_ctx* c, int R) {
             for (size_t j = 0; j < n; ++j) {
                 bundle_ctx* m = c->members[k0 + j];
                 P->a[j] = make_step_args(m, kModeAdvectResample, R, 1 - R);
-                P->blk[j + 1] = P->blk[j] + (int32_t)((m->E + m->eb - 1) / m->eb);
+                P->blk[j + 1] = P->blk[j] + (int32_t)step_ctas(m->E, m->eb);
             }
             if (launch_step_batch(kModeAdvectResample, c->members[0]->p.rho_dtype, *P,
                                   c->cap_stream) != cudaSuccess ||
@@ -1070,6 +1080,9 @@ bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
     if (!c) return BUNDLE_EINVAL;
     if (c->is_member)
         return fail(&c->err, BUNDLE_ESTATE, "a batch member iterates with its batch");
+    if (c->split_state != 0)
+        return fail(&c->err, BUNDLE_ESTATE, "a run of bundle_points_step is open: end it with "
+                    "BUNDLE_STEP_LAST first");
     if (n_iters < 0) return fail(&c->err, BUNDLE_EINVAL, "n_iters must be >= 0");
     if (n_iters == 0) return BUNDLE_OK;
     DeviceGuard dg(c->device);
@@ -1082,6 +1095,96 @@ bundle_status bundle_iterate(bundle_ctx* c, int32_t n_iters) {
         return s;
     }
     return iterate_single(c, n_iters);
+}
+
+// ------------------------------------------------------------------ split form
+// One graph's edges divided over several contexts (one per process or GPU): each
+// context runs the per-edge stages -- advection, Laplacian smoothing, resampling and
+// the splat -- on its own edges, and the histogram, the only state that couples
+// edges, is summed over the contexts between the splat and the box passes. Integer
+// addition is exact and order-free, so every context then holds the histogram of the
+// whole graph and the run equals one context over all edges bit for bit. (Sec. 4
+// splits the edges of one graph over CPU threads the same way.)
+
+static bundle_status split_checks(bundle_ctx* c, const char* what) {
+    if (!c->members.empty() || c->is_member)
+        return fail(&c->err, BUNDLE_ESTATE, "%s: batches run whole iterations", what);
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_points_step(bundle_ctx* c, int32_t flags) {
+    if (!c) return BUNDLE_EINVAL;
+    if (bundle_status s = split_checks(c, "bundle_points_step")) return s;
+    if (flags & ~BUNDLE_STEP_LAST)
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_points_step: unknown flags %d", flags);
+    if (c->split_state == 1)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_points_step: run bundle_density_step on the "
+                    "(summed) histogram first");
+    DeviceGuard dg(c->device);
+    bundle_status s = ensure_schedule(c, c->iteration + 1);
+    if (s != BUNDLE_OK) return s;
+    if (c->split_state == 0) {
+        if (flags & BUNDLE_STEP_LAST)
+            return fail(&c->err, BUNDLE_EINVAL, "bundle_points_step: a run opens without "
+                        "BUNDLE_STEP_LAST");
+        // the start of a run: resample and splat the current polylines
+        CUDA_TRY(&c->err, launch_set_iter(c->d_iter, c->iteration, c->stream));
+        if ((s = run_step(c, kModeResample, c->cur_P, 1 - c->cur_P)) != BUNDLE_OK) return s;
+        c->split_R = 1 - c->cur_P;
+        c->split_state = 1;
+        return BUNDLE_OK;
+    }
+    // advect on this iteration's density; resample and splat for the next one unless last
+    const int R = c->split_R;
+    const bool last = (flags & BUNDLE_STEP_LAST) != 0;
+    if ((s = run_step(c, last ? kModeAdvect : kModeAdvectResample, R, 1 - R)) != BUNDLE_OK) return s;
+    CUDA_TRY(&c->err, launch_advance_iter(c->d_iter, c->stream));
+    c->iteration += 1;
+    if (last) {
+        c->cur_P = 1 - R;
+        c->cur_R = R;
+        c->split_state = 0;
+    } else {
+        c->split_R = 1 - R;
+        c->split_state = 1;
+    }
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_density_step(bundle_ctx* c) {
+    if (!c) return BUNDLE_EINVAL;
+    if (bundle_status s = split_checks(c, "bundle_density_step")) return s;
+    if (c->split_state != 1)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_density_step: no splatted histogram is "
+                    "waiting (call bundle_points_step first)");
+    DeviceGuard dg(c->device);
+    bundle_status s = run_filter(c);
+    if (s != BUNDLE_OK) return s;
+    c->split_state = 2;
+    c->have_density = true;
+    return BUNDLE_OK;
+}
+
+bundle_status bundle_set_histogram(bundle_ctx* c, const uint32_t* src, int32_t flags) {
+    if (!c) return BUNDLE_EINVAL;
+    if (bundle_status s = split_checks(c, "bundle_set_histogram")) return s;
+    if (!src) return fail(&c->err, BUNDLE_EINVAL, "bundle_set_histogram: src is NULL");
+    if (flags & ~BUNDLE_INPUT_DEVICE)
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_set_histogram: unknown flags %d", flags);
+    if (c->split_state != 1)
+        return fail(&c->err, BUNDLE_ESTATE, "bundle_set_histogram: only between "
+                    "bundle_points_step and bundle_density_step");
+    DeviceGuard dg(c->device);
+    const size_t C = (size_t)c->G * c->H * c->W;
+    // copy 0 takes the histogram, the other copies are cleared: the row passes sum them
+    CUDA_TRY(&c->err, cudaMemcpyAsync(c->hist, src, C * sizeof(uint32_t),
+                                      (flags & BUNDLE_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                    : cudaMemcpyHostToDevice,
+                                      c->stream));
+    CUDA_TRY(&c->err, cudaMemsetAsync(c->hist + C, 0, (kHistCopies - 1) * C * sizeof(uint32_t),
+                                      c->stream));
+    if (!(flags & BUNDLE_INPUT_DEVICE)) CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    return BUNDLE_OK;
 }
 
 bundle_status bundle_init_batch(bundle_ctx** out, int32_t n_graphs, const bundle_graph_desc* graphs,
@@ -1279,7 +1382,7 @@ static bundle_status autotune_one(bundle_ctx* c) {
     if (s != BUNDLE_OK) return s;
     int32_t best_eb = c->eb;
     float best = 3.4e38f;
-    for (int32_t eb = 16; eb <= kEdgesPerBlock; eb *= 2) {
+    for (int32_t eb = 4; eb <= kMaxEdgesPerWarp; eb *= 2) {
         for (int rep = 0; rep < 2; ++rep) {
             if ((s = probe_layout(c, t, eb)) != BUNDLE_OK || (s = probe_prefix(c)) != BUNDLE_OK)
                 return s;
@@ -1296,7 +1399,7 @@ static bundle_status autotune_one(bundle_ctx* c) {
 }
 
 // A batch runs its graphs side by side, so the block size is chosen for the whole batch:
-// each policy (every graph at its size rule, or every graph at 16, 32, 64 or 128 edges
+// each policy (every graph at its size rule, or every graph at 4, 8, 16 or 32 edges
 // per block) times the fused step of all graphs together, forked from the batch stream
 // and joined back (best of two). The filter tiles are then tuned per graph.
 static bundle_status autotune_batch(bundle_ctx* c) {
@@ -1312,11 +1415,11 @@ static bundle_status autotune_batch(bundle_ctx* c) {
     }
     int best_policy = 0;
     float best = 3.4e38f;
-    for (int policy = 0; policy <= 4; ++policy) {  // 0: size rule, 1..4: 16 << (policy - 1)
+    for (int policy = 0; policy <= 4; ++policy) {  // 0: size rule, 1..4: 4 << (policy - 1)
         for (int rep = 0; rep < 2; ++rep) {
             for (size_t k = 0; k < n; ++k) {
                 bundle_ctx* m = c->members[k];
-                const int32_t eb = policy == 0 ? rule[k] : (16 << (policy - 1));
+                const int32_t eb = policy == 0 ? rule[k] : (4 << (policy - 1));
                 if ((s = probe_layout(m, t[k], eb)) != BUNDLE_OK || (s = probe_prefix(m)) != BUNDLE_OK)
                     return s;
             }
@@ -1337,7 +1440,7 @@ static bundle_status autotune_batch(bundle_ctx* c) {
     for (size_t k = 0; k < n; ++k) {
         bundle_ctx* m = c->members[k];
         if ((s = tune_filter(m)) != BUNDLE_OK) return s;
-        const int32_t eb = best_policy == 0 ? rule[k] : (16 << (best_policy - 1));
+        const int32_t eb = best_policy == 0 ? rule[k] : (4 << (best_policy - 1));
         if ((s = probe_end(m, t[k], eb)) != BUNDLE_OK) return s;
     }
     for (cudaGraphExec_t& g : c->bexec)
@@ -1352,8 +1455,8 @@ bundle_status bundle_set_tiles(bundle_ctx* c, int32_t eb, int32_t row_mode, int3
     if (!c) return BUNDLE_EINVAL;
     if (!c->members.empty() || c->is_member)
         return fail(&c->err, BUNDLE_ESTATE, "bundle_set_tiles: set the tiles of single contexts");
-    if (eb != 0 && (eb < 16 || eb > kEdgesPerBlock || (eb & (eb - 1)) != 0))
-        return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: eb must be 0, 16, 32, 64 or 128");
+    if (eb != 0 && (eb < 4 || eb > kMaxEdgesPerWarp || (eb & (eb - 1)) != 0))
+        return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: eb must be 0, 4, 8, 16 or 32");
     if (!rowbox_mode_valid(row_mode, c->W))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: row variant %d does not exist for "
                     "width %d", row_mode, c->W);
@@ -1521,6 +1624,8 @@ bundle_status bundle_render(bundle_ctx* c, const bundle_render_params* rp,
         a.log_width = rp->log_width;
         int n_sm = 0;
         e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device);
+        if (e == cudaSuccess && !(rp->rho_ref > 0.0f))
+            e = launch_rho_from_quads(c->p.rho_dtype, filter_args(c), c->stream);
         if (e == cudaSuccess)
             e = launch_render(c->p.rho_dtype, a, c->rho, (int64_t)c->G * c->H * c->W,
                               !(rp->rho_ref > 0.0f), n_sm, c->stream);
@@ -1622,7 +1727,8 @@ bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int6
     if (!c->members.empty())
         return fail(&c->err, BUNDLE_ESTATE, "fetch a batch's graphs through bundle_batch_member");
     if (!dst) return fail(&c->err, BUNDLE_EINVAL, "dst is NULL");
-    if (!c->have_density) return fail(&c->err, BUNDLE_ESTATE, "no iteration has run");
+    if (!c->have_density && !(which == BUNDLE_DENSITY_HIST && c->split_state == 1))
+        return fail(&c->err, BUNDLE_ESTATE, "no iteration has run");
     const size_t C = (size_t)c->G * c->H * c->W;
     const void* src;
     size_t bytes;
@@ -1639,6 +1745,8 @@ bundle_status bundle_fetch_density(bundle_ctx* c, int32_t which, void* dst, int6
     if (bundle_status fs = check_device_flag(c)) return fs;
     if (which == BUNDLE_DENSITY_HIST)
         CUDA_TRY(&c->err, launch_fold_hist(c->hist, (int64_t)C, kHistCopies, c->stream));
+    if (which == BUNDLE_DENSITY_RHO)
+        CUDA_TRY(&c->err, launch_rho_from_quads(c->p.rho_dtype, filter_args(c), c->stream));
     CUDA_TRY(&c->err, cudaMemcpyAsync(dst, src, bytes,
                                       (flags & BUNDLE_FETCH_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                     : cudaMemcpyDeviceToHost,

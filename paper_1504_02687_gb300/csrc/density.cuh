@@ -52,13 +52,17 @@ __device__ __forceinline__ Frame frame_of(float x, float y, int W, int H) {
     return f;
 }
 
+// Bilinear density of the 2x2 quad q at fractions (fu, fv).
+__device__ __forceinline__ float bilinear(float4 q, float fu, float fv) {
+    return lerp_rn(lerp_rn(q.x, q.y, fu), lerp_rn(q.z, q.w, fu), fv);
+}
+
 // Bilinear density of one layer's quad map at (x, y).
 template <typename T>
 __device__ __forceinline__ float density_at(const T* __restrict__ Q, int W, int H, float x,
                                             float y) {
     Frame f = frame_of(x, y, W, H);
-    float4 q = load_quad(Q, (int64_t)(f.b0 + 2) * (W + kQuadPad) + (f.a0 + 2));
-    return lerp_rn(lerp_rn(q.x, q.y, f.fu), lerp_rn(q.z, q.w, f.fu), f.fv);
+    return bilinear(load_quad(Q, (int64_t)(f.b0 + 2) * (W + kQuadPad) + (f.a0 + 2)), f.fu, f.fv);
 }
 
 __device__ __forceinline__ float clamp_pos(float v, int n) {

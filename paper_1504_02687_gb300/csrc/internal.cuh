@@ -10,15 +10,24 @@
 namespace heb {
 
 // Point layout. Edges live in blocks of `eb` consecutive (spatially sorted)
-// slots, eb <= kEdgesPerBlock chosen per context; block b owns the point region
+// slots, eb <= kMaxEdgesPerWarp chosen per context; block b owns the point region
 // [b * eb * cap, (b+1) * eb * cap) of a float2 buffer, and packs its edges'
 // polylines back to back inside it, in slot order. Only the per-slot point
-// counts are stored: a block recovers its edges' offsets with one scan.
+// counts are stored: the warp that owns a block recovers its edges' offsets with
+// one warp scan. Buffers are sized for blocks of kEdgesPerBlock slots, which
+// covers every eb that divides it.
 constexpr int kEdgesPerBlock = 128;
-constexpr int kStepThreads = 256;
-constexpr int kBatchPoints = 2048;  // points staged in shared memory per batch
-constexpr int kMaxCap = 64;         // largest polyline (n_fixed or n_max): two points per lane
+constexpr int kMaxEdgesPerWarp = 32;  // one slot per lane
+constexpr int kStepWarps = 4;         // warps per CTA of the step kernel, one block each
+constexpr int kStepThreads = 32 * kStepWarps;
+constexpr int kStage = 128;           // points of whole polylines staged per warp
+constexpr int kMaxCap = 64;           // largest polyline (n_fixed or n_max): two points per lane
 constexpr float kEdgeGuard = 0.0009765625f;  // positions stay below W - 2^-10
+// CTAs of one step launch over E edges in blocks of eb.
+__host__ __device__ inline int64_t step_ctas(int64_t E, int eb) {
+    const int64_t blocks = (E + eb - 1) / eb;
+    return (blocks + kStepWarps - 1) / kStepWarps;
+}
 // The splat writes into kHistCopies copies of the histogram (block b into copy
 // b mod kHistCopies) and the row-pass kernel sums them as it reads: bundled
 // polylines put many points on the same cells, and atomics on one address
@@ -38,11 +47,11 @@ struct StepArgs {
     float2* pts_out;         // output polylines (block layout)
     const int32_t* group;    // [E] per slot
     const int32_t* weight;   // [E] per slot
-    const void* quads;       // [G][H+3][W+3] 2x2 density quads (see QuadMap), rho type
+    const void* quads;       // [G][H+3][W+3] density quads (see below), rho type x 4
     uint32_t* hist;          // [G][H][W] histogram accumulated by the splat
     unsigned long long* n_splat;  // running count of splatted points
     int64_t E;
-    int32_t eb;              // edges per block (<= kEdgesPerBlock)
+    int32_t eb;              // edges per block (<= kMaxEdgesPerWarp)
     int32_t cap;             // points per slot of the region (n_fixed or n_max)
     int32_t W, H, G;
     float h;                 // step magnitude h_i (used when h_sched is null)
@@ -65,7 +74,7 @@ struct RenderArgs {
     const float2* pts;       // current polylines (block layout)
     const int32_t* group;    // [E] per slot
     const int32_t* weight;   // [E] per slot
-    const void* quads;       // density quads of the last iteration (rho type)
+    const void* quads;       // density quads of the last iteration (rho type x 4)
     unsigned long long* depth;  // [G][Hi][Wi]: optical depth per bin (2^-20 units)
     unsigned int* rho_ref;   // density mapped to the full width, as float bits
     int64_t E;
@@ -91,7 +100,7 @@ struct FilterArgs {
     int32_t hist_copies;
     void* Y;               // [G][H][W] row-filtered workspace (sum type)
     void* S;               // [G][H][W] smoothed sums (sum type)
-    void* rho;             // [G][H][W] density (rho type)
+    void* rho;             // [G][H][W] density (rho type), filled from the quads on demand
     void* quads;           // [G][H+3][W+3] density quads (rho type x 4)
     int32_t G, H, W, r, passes;
     const int64_t* mix;    // optional G x G integer interaction numerators (row-major)
@@ -103,13 +112,13 @@ struct FilterArgs {
     int32_t row_mode;      // row pass: 0 by width, 1 register-resident rows, 2 shared-memory rows
 };
 
-// Density quads. The gather side of the iteration reads the density through a
-// quad map: entry (a, b), for a in [-2, W] and b in [-2, H], holds the four
-// values {E(a,b), E(a+1,b), E(a,b+1), E(a+1,b+1)} of the reflection-extended
-// map E(a, b) = rho(refl(a), refl(b)) at quad index (b + 2) * (W + 3) + (a + 2).
-// One quad is the whole 2x2 footprint of a bilinear lookup; four quads hold
-// the 12 texels of the gradient stencil. No index reflection happens on the
-// gather side.
+// Density quads. The gather side of the iteration reads each layer's density through
+// a quad map: entry (a, b), for a in [-2, W] and b in [-2, H], holds the four values
+// {E(a,b), E(a+1,b), E(a,b+1), E(a+1,b+1)} of the reflection-extended map
+// E(a, b) = rho(refl(a), refl(b)) at quad index (b + 2) * (W + 3) + (a + 2). One
+// quad is the whole 2x2 footprint of a bilinear lookup (one 16-byte load for FP32
+// densities, 8 bytes for 16-bit ones); four quads hold the 12 cells of the gradient
+// stencil. No index reflection happens on the gather side.
 constexpr int kQuadPad = 3;
 __host__ __device__ inline int64_t quad_elems(int W, int H) {
     return (int64_t)(W + kQuadPad) * (H + kQuadPad);
@@ -122,8 +131,10 @@ cudaError_t launch_step_batch(int mode, int rho_dtype, const BatchStepArgs& P, c
 cudaError_t launch_advance_batch(const BatchStepArgs& P, cudaStream_t st);
 cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st);
-cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st);
-cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st);
+// Layer mix (Eq. 3 / Eq. 4) of the sums straight into the density quad map.
+cudaError_t launch_mix_quads(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st);
+// The density stack [G][H][W] (a.rho) from the quad map (for fetches and the renderer).
+cudaError_t launch_rho_from_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st);
 // Fold histogram copies 1.. into copy 0 (their sum is unchanged), n cells per copy.
 cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t st);
 // Renderer: capsule fragments into the accumulators (after the stack maximum of rho

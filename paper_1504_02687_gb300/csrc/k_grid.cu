@@ -85,31 +85,30 @@ __global__ void k_rowbox(const uint32_t* __restrict__ hist, int copies, TS* __re
 
 // Row passes for rows whose lane chunk c = ceil(W / 32) is C (8, 16 or 32): lane l
 // owns [l*C, l*C + C) and keeps a pass's outputs in registers until the warp has
-// read the pass's input, so a row needs one shared buffer. A table built once per
-// CTA maps every window index t in [-r-1, W+r] to the shared slot of refl(t); the
-// buffer and the table both skip one slot after every C entries, so the 32 lanes,
-// C apart, hit 32 different banks.
+// read the pass's input, so a row needs one shared buffer. The buffer holds the row
+// with a border of `halo` >= r + 1 cells on each side filled with the reflected
+// values (refreshed after every pass), so every window reads its cells directly,
+// with no index reflection. A slot is skipped after every C cells, so the 32 lanes,
+// C apart, hit different banks.
 constexpr int kRowWarps = 8;
 
 template <int C>
-__device__ __forceinline__ int padded(int k) { return k + k / C; }
+__host__ __device__ __forceinline__ int padded(int k) { return k + k / C; }
 
 template <typename TS, int C>
 __global__ void __launch_bounds__(32 * kRowWarps)
     k_rowbox_reg(const uint32_t* __restrict__ hist, int copies, TS* __restrict__ Y, int G, int H,
-                 int W, int r, int passes) {
+                 int W, int r, int passes, int halo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LG = C == 8 ? 3 : C == 16 ? 4 : 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int stride = padded<C>(W) + 1;
+    const int stride = padded<C>(W + 2 * halo) + 1;
     TS* buf = reinterpret_cast<TS*>(smem_raw) + (size_t)warp * stride;
-    int* tab = reinterpret_cast<int*>(reinterpret_cast<TS*>(smem_raw) + (size_t)kRowWarps * stride);
-    const int ntab = W + 2 * r + 2;  // k = t + r + 1 for t = -r-1 .. W+r
-    for (int k = threadIdx.x; k < ntab; k += blockDim.x)
-        tab[padded<C>(k)] = padded<C>(reflect_index(k - r - 1, W));
-    __syncthreads();
     const int g = blockIdx.y;
     const int v = blockIdx.x * kRowWarps + warp;
     if (v >= H) return;
+    // cell t (t in [-halo, W + halo)) lives in slot padded(t + halo)
+    auto slot = [&](int t) { return padded<C>(t + halo); };
     const size_t base = ((size_t)g * H + v) * W;
     const size_t stride_copy = (size_t)G * H * W;
     if ((W & 3) == 0 && copies == 2) {
@@ -131,10 +130,10 @@ __global__ void __launch_bounds__(32 * kRowWarps)
             const int x4 = lane + 32 * it;
             if (x4 < (W >> 2)) {
                 const int x = 4 * x4;
-                buf[padded<C>(x)] = (TS)(u[it].x + w[it].x);
-                buf[padded<C>(x + 1)] = (TS)(u[it].y + w[it].y);
-                buf[padded<C>(x + 2)] = (TS)(u[it].z + w[it].z);
-                buf[padded<C>(x + 3)] = (TS)(u[it].w + w[it].w);
+                buf[slot(x)] = (TS)(u[it].x + w[it].x);
+                buf[slot(x + 1)] = (TS)(u[it].y + w[it].y);
+                buf[slot(x + 2)] = (TS)(u[it].z + w[it].z);
+                buf[slot(x + 3)] = (TS)(u[it].w + w[it].w);
             }
         }
     } else if ((W & 3) == 0) {
@@ -149,32 +148,42 @@ __global__ void __launch_bounds__(32 * kRowWarps)
                 u.w += w.w;
             }
             const int x = 4 * x4;
-            buf[padded<C>(x)] = (TS)u.x;
-            buf[padded<C>(x + 1)] = (TS)u.y;
-            buf[padded<C>(x + 2)] = (TS)u.z;
-            buf[padded<C>(x + 3)] = (TS)u.w;
+            buf[slot(x)] = (TS)u.x;
+            buf[slot(x + 1)] = (TS)u.y;
+            buf[slot(x + 2)] = (TS)u.z;
+            buf[slot(x + 3)] = (TS)u.w;
         }
     } else {
         for (int x = lane; x < W; x += 32) {
             TS u = (TS)hist[base + x];
             for (int k = 1; k < copies; ++k) u += (TS)hist[k * stride_copy + base + x];
-            buf[padded<C>(x)] = u;
+            buf[slot(x)] = u;
         }
     }
-    __syncwarp();
+    // the reflected border: cells -r-1 .. -1 and W .. W+r
+    auto refresh_border = [&]() {
+        __syncwarp();
+        for (int k = lane; k < 2 * (r + 1); k += 32) {
+            const int t = k <= r ? -1 - k : W + (k - r - 1);
+            buf[slot(t)] = buf[slot(reflect_index(t, W))];
+        }
+        __syncwarp();
+    };
+    refresh_border();
     const int i0 = lane * C;
     const int len = max(0, min(C, W - i0));
-    const int own = padded<C>(i0);
+    // lane's chunk: cell i0 + x is bl[x + floor(x / C)] (i0 + halo is a multiple of C)
+    TS* bl = buf + slot(i0);
     TS out[C];
     for (int p = 0; p < passes; ++p) {
         if (len > 0) {
             TS s = 0;
-            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t) s += buf[tab[padded<C>(t + r + 1)]];
+            for (int x = -1 - r; x <= -1 + r; ++x) s += bl[x + (x >> LG)];
 #pragma unroll
             for (int q = 0; q < C; ++q) {
                 if (q < len) {
-                    const int k = i0 + q + r + 1;  // table position of t = i0 + q
-                    s += buf[tab[padded<C>(k + r)]] - buf[tab[padded<C>(k - r - 1)]];
+                    const int xa = q + r, xs = q - r - 1;
+                    s += bl[xa + (xa >> LG)] - bl[xs + (xs >> LG)];
                     out[q] = s;
                 }
             }
@@ -182,16 +191,19 @@ __global__ void __launch_bounds__(32 * kRowWarps)
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < C; ++q)
-            if (q < len) buf[own + q] = out[q];
-        __syncwarp();
+            if (q < len) bl[q + (q >> LG)] = out[q];
+        refresh_border();
     }
-    for (int x = lane; x < W; x += 32) Y[base + x] = buf[padded<C>(x)];
+    for (int x = lane; x < W; x += 32) Y[base + x] = buf[slot(x)];
 }
+
+// border width of the register row pass: r + 1 rounded up to a whole chunk
+inline int row_halo(int r, int C) { return (r + 1 + C - 1) / C * C; }
 
 template <typename TS, int C>
 cudaError_t rowbox_reg_t(const FilterArgs& a, cudaStream_t st) {
-    const size_t smem = (size_t)kRowWarps * (a.W + a.W / C + 1) * sizeof(TS) +
-                        (size_t)(a.W + 2 * a.r + 2 + (a.W + 2 * a.r + 2) / C + 1) * 4;
+    const int halo = row_halo(a.r, C);
+    const size_t smem = (size_t)kRowWarps * (padded<C>(a.W + 2 * halo) + 1) * sizeof(TS);
     auto kern = k_rowbox_reg<TS, C>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
@@ -199,40 +211,41 @@ cudaError_t rowbox_reg_t(const FilterArgs& a, cudaStream_t st) {
     dim3 grid((unsigned)((a.H + kRowWarps - 1) / kRowWarps), (unsigned)a.G);
     kern<<<grid, 32 * kRowWarps, smem, st>>>(a.hist, a.hist_copies < 1 ? 1 : a.hist_copies,
                                               static_cast<TS*>(a.Y), a.G, a.H, a.W, a.r,
-                                              a.passes);
+                                              a.passes, halo);
     return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- column passes
 // One CTA per strip of STRIP columns of one layer, the whole column height in
-// shared memory. Thread (j, ch) owns column j and the 16-row chunk ch; its 16
-// outputs of a pass stay in registers until the whole CTA has read the pass's
-// input. A pad row after every chunk spreads the chunks over the banks. The
-// strip narrows (8, 4, 2 columns) as the height grows so that a CTA keeps 256
-// threads and the strip fits in shared memory.
+// shared memory with a border of `halo` >= r + 1 rows on each side holding the
+// reflected rows (refreshed after every pass), so every window reads its rows
+// directly. Thread (j, ch) owns column j and the 16-row chunk ch; its 16 outputs of
+// a pass stay in registers until the whole CTA has read the pass's input. A pad row
+// after every chunk spreads the chunks over the banks. The strip narrows (8, 4, 2
+// columns) as the height grows so that a CTA keeps its threads and the strip fits
+// in shared memory.
 constexpr int kChunk = 16;
 constexpr int kColThreads = 512;
+
+// border rows of the column pass: r + 1 rounded up to a whole chunk
+inline int col_halo(int r) { return (r + 1 + kChunk - 1) / kChunk * kChunk; }
+inline size_t colbox_smem(int H, int r, int strip, int sum_bytes) {
+    const int rows = H + 2 * col_halo(r);
+    return (size_t)(rows + rows / kChunk + 1) * strip * sum_bytes;
+}
 
 template <typename TS, int STRIP>
 __global__ void __launch_bounds__(kColThreads)
     k_colbox(const TS* __restrict__ Y, TS* __restrict__ S, int G, int H, int W, int r,
-             int passes) {
+             int passes, int halo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TS* buf = reinterpret_cast<TS*>(smem_raw);
-    const int nch = (H + kChunk - 1) / kChunk;
-    // tab[k + k/32], k = t + r + 1: shared offset of row refl(t) (padded, times STRIP) for
-    // t = -r-1 .. H+r; the skipped slot every 32 entries keeps the chunks' lookups apart
-    int* tab = reinterpret_cast<int*>(buf + (size_t)(H + nch) * STRIP);
-    const int ntab = H + 2 * r + 2;
-    for (int k = threadIdx.x; k < ntab; k += blockDim.x) {
-        const int q = reflect_index(k - r - 1, H);
-        tab[k + k / kChunk] = (q + q / kChunk) * STRIP;
-    }
     const int g = blockIdx.y;
     const int x0 = blockIdx.x * STRIP;
     const int j = threadIdx.x % STRIP, ch = threadIdx.x / STRIP;
     const size_t lay = (size_t)g * H * W;
-    auto prow = [](int row) { return row + row / kChunk; };
+    // row t (t in [-halo, H + halo)) of the strip starts at element prow(t) * STRIP
+    auto prow = [&](int t) { const int k = t + halo; return k + k / kChunk; };
     // the strip's rows are copied asynchronously straight into shared memory, all in
     // flight at once: 16-byte pieces when rows and strips are 16-byte aligned, else one
     // element per copy; columns past the width are zero-filled
@@ -262,35 +275,44 @@ __global__ void __launch_bounds__(kColThreads)
         }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
+    // the reflected border: rows -r-1 .. -1 and H .. H+r of every column of the strip
+    auto refresh_border = [&]() {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * (r + 1) * STRIP; k += blockDim.x) {
+            const int e = k / STRIP, c = k % STRIP;
+            const int t = e <= r ? -1 - e : H + (e - r - 1);
+            buf[prow(t) * STRIP + c] = buf[prow(reflect_index(t, H)) * STRIP + c];
+        }
+        __syncthreads();
+    };
+    refresh_border();
     const int i0 = ch * kChunk;
     const int len = max(0, min(kChunk, H - i0));
-    auto tl = [&](int t) { const int k = t + r + 1; return tab[k + k / kChunk]; };
-    const TS* col = buf + j;
+    // row i0 + x of column j: col[(x + floor(x / 16)) * STRIP] (i0 + halo is a whole chunk)
+    TS* col = buf + (size_t)prow(i0) * STRIP + j;
     TS out[kChunk];
     for (int p = 0; p < passes; ++p) {
         if (len > 0) {
             TS s = 0;
-            for (int t = i0 - 1 - r; t <= i0 - 1 + r; ++t) s += col[tl(t)];
+            for (int x = -1 - r; x <= -1 + r; ++x) s += col[(x + (x >> 4)) * STRIP];
 #pragma unroll
             for (int q = 0; q < kChunk; ++q) {
                 if (q < len) {
-                    const int i = i0 + q;
-                    s += col[tl(i + r)] - col[tl(i - r - 1)];
+                    const int xa = q + r, xs = q - r - 1;
+                    s += col[(xa + (xa >> 4)) * STRIP] - col[(xs + (xs >> 4)) * STRIP];
                     out[q] = s;
                 }
             }
         }
         __syncthreads();
-        TS* mine = buf + (size_t)prow(i0) * STRIP + j;
 #pragma unroll
         for (int q = 0; q < kChunk; ++q)
-            if (q < len) mine[q * STRIP] = out[q];
-        __syncthreads();
+            if (q < len) col[q * STRIP] = out[q];
+        refresh_border();
     }
     for (int idx = threadIdx.x; idx < H * STRIP; idx += blockDim.x) {
-        int row = idx / STRIP, col = idx % STRIP, x = x0 + col;
-        if (x < W) S[lay + (size_t)row * W + x] = buf[prow(row) * STRIP + col];
+        int row = idx / STRIP, c = idx % STRIP, x = x0 + c;
+        if (x < W) S[lay + (size_t)row * W + x] = buf[prow(row) * STRIP + c];
     }
 }
 
@@ -298,7 +320,9 @@ __global__ void __launch_bounds__(kColThreads)
 // Eq. 3 / Eq. 4 after smoothing: with alpha = p / q and B groups,
 //   rho_l = (S_l - alpha / (B - 1) * sum_{b != l} S_b) / s^k
 //         = ((q (B-1) + p) S_l - p T) / (q (B-1) s^k),  T = sum_b S_b,
-// whose numerator is an exact int64; one rounding gives the stored density.
+// whose numerator is an exact int64; one rounding gives the stored density. A
+// general interaction matrix (Eq. 3) gives rho_l = (sum_b num[l, b] S_b) / (den s^k),
+// its numerator exact as well.
 template <typename R>
 __device__ __forceinline__ R to_rho(float v);
 template <>
@@ -310,27 +334,18 @@ __device__ __forceinline__ __nv_bfloat16 to_rho<__nv_bfloat16>(float v) {
 template <>
 __device__ __forceinline__ __half to_rho<__half>(float v) { return __float2half_rn(v); }
 
-template <typename TS, typename R>
-__global__ void k_combine(const TS* __restrict__ S, R* __restrict__ rho, int G, int64_t C,
-                          int64_t mix_self, int64_t mix_all, float den) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= C) return;
-    if (G == 1) {
-        long long v = (long long)S[idx];
-        rho[idx] = to_rho<R>(__fdiv_rn(__ll2float_rn(v), den));
-        return;
-    }
-    long long T = 0;
-    for (int g = 0; g < G; ++g) T += (long long)S[(size_t)g * C + idx];
-    for (int g = 0; g < G; ++g) {
-        long long num = mix_self * (long long)S[(size_t)g * C + idx] - mix_all * T;
-        rho[(size_t)g * C + idx] = to_rho<R>(__fdiv_rn(__ll2float_rn(num), den));
-    }
-}
+// ------------------------------------------------ layer mix into the density quads
+// The layer mix is computed straight into the quad map the gather side reads, with no
+// density stack in between. A CTA takes a tile of kMqX x kMqY quads (quad (a, b), a in
+// [-2, W], b in [-2, H]) of every layer. First one thread per cell of the tile's
+// footprint -- cells a0 .. a0 + kMqX and b0 .. b0 + kMqY of the reflection-extended
+// grid -- mixes all layers at its source cell (exact integer numerator, one rounding)
+// into shared memory; then the tile's quads of every layer are assembled from there and
+// written as whole vectors. The density stack itself is extracted from the quads only
+// when fetched.
+constexpr int kMqX = 32, kMqY = 8, kMqThreads = 256;
+constexpr int kMqFX = kMqX + 1, kMqF = kMqFX * (kMqY + 1);
 
-// ------------------------------------------------------------- density quads
-// Quad (a, b), a in [-2, W], b in [-2, H]: the 2x2 block of the reflection-
-// extended density with top-left corner (a, b), stored as one vector.
 template <typename R>
 __device__ __forceinline__ uint32_t pack2(R lo, R hi) {
     unsigned short l = *reinterpret_cast<unsigned short*>(&lo);
@@ -338,30 +353,98 @@ __device__ __forceinline__ uint32_t pack2(R lo, R hi) {
     return (uint32_t)l | ((uint32_t)h << 16);
 }
 
-template <typename R>
-__global__ void k_quads(const R* __restrict__ rho, R* __restrict__ quads, int G, int H, int W) {
+inline size_t mix_quads_smem(int G, bool matrix, int rho_bytes) {
+    const size_t rho = ((size_t)G * kMqF * rho_bytes + 15) / 16 * 16;
+    return rho + (matrix ? (size_t)G * G * sizeof(long long) : 0);
+}
+
+template <typename TS, typename R>
+__global__ void __launch_bounds__(kMqThreads)
+    k_mix_quads(const TS* __restrict__ S, R* __restrict__ quads, int G, int H, int W,
+                int64_t mix_self, int64_t mix_all, const int64_t* __restrict__ mix, float den) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* s_rho = reinterpret_cast<R*>(smem_raw);  // [G][kMqF]
+    long long* s_num = reinterpret_cast<long long*>(
+        smem_raw + ((size_t)G * kMqF * sizeof(R) + 15) / 16 * 16);  // G x G (general matrix)
+    const int tid = threadIdx.x;
+    const int a0 = -2 + (int)blockIdx.x * kMqX, b0 = -2 + (int)blockIdx.y * kMqY;
+    const int64_t C = (int64_t)H * W;
+    if (mix)
+        for (int k = tid; k < G * G; k += blockDim.x) s_num[k] = mix[k];
+    __syncthreads();
+    for (int f = tid; f < kMqF; f += blockDim.x) {
+        // footprint cell -> its source cell (cells past the last quad are clamped onto it:
+        // computed, never used)
+        const int a = min(a0 + f % kMqFX, W + 1), b = min(b0 + f / kMqFX, H + 1);
+        const int64_t c = (int64_t)reflect_index(b, H) * W + reflect_index(a, W);
+        if (mix) {
+            for (int l = 0; l < G; ++l) {
+                long long acc = 0;
+                for (int g = 0; g < G; ++g)
+                    acc += s_num[l * G + g] * (long long)S[(size_t)g * C + c];
+                s_rho[l * kMqF + f] = to_rho<R>(__fdiv_rn(__ll2float_rn(acc), den));
+            }
+        } else if (G == 1) {
+            s_rho[f] = to_rho<R>(__fdiv_rn(__ll2float_rn((long long)S[c]), den));
+        } else {
+            long long T = 0;
+            for (int g = 0; g < G; ++g) T += (long long)S[(size_t)g * C + c];
+            for (int l = 0; l < G; ++l) {
+                const long long num = mix_self * (long long)S[(size_t)l * C + c] - mix_all * T;
+                s_rho[l * kMqF + f] = to_rho<R>(__fdiv_rn(__ll2float_rn(num), den));
+            }
+        }
+    }
+    __syncthreads();
     const int64_t Wq = W + kQuadPad, QC = Wq * (H + kQuadPad);
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)G * QC) return;
-    const int64_t g = idx / QC, rem = idx % QC;
-    const int b = (int)(rem / Wq) - 2, a = (int)(rem % Wq) - 2;
-    const R* L = rho + g * (int64_t)H * W;
-    const int r0 = reflect_index(b, H) * W, r1 = reflect_index(b + 1, H) * W;
-    const int c0 = reflect_index(a, W), c1 = reflect_index(a + 1, W);
-    R e00 = L[r0 + c0], e10 = L[r0 + c1], e01 = L[r1 + c0], e11 = L[r1 + c1];
-    if constexpr (sizeof(R) == 4) {
-        reinterpret_cast<float4*>(quads)[idx] = make_float4(e00, e10, e01, e11);
-    } else {
-        reinterpret_cast<uint2*>(quads)[idx] = make_uint2(pack2(e00, e10), pack2(e01, e11));
+    for (int e = tid; e < G * kMqX * kMqY; e += blockDim.x) {
+        const int l = e / (kMqX * kMqY), qq = e % (kMqX * kMqY);
+        const int qx = qq % kMqX, qy = qq / kMqX;
+        const int a = a0 + qx, b = b0 + qy;
+        if (a > W || b > H) continue;
+        const R* r = s_rho + l * kMqF + qy * kMqFX + qx;
+        const R e00 = r[0], e10 = r[1], e01 = r[kMqFX], e11 = r[kMqFX + 1];
+        const int64_t idx = (int64_t)l * QC + (int64_t)(b + 2) * Wq + (a + 2);
+        if constexpr (sizeof(R) == 4) {
+            reinterpret_cast<float4*>(quads)[idx] = make_float4(e00, e10, e01, e11);
+        } else {
+            reinterpret_cast<uint2*>(quads)[idx] = make_uint2(pack2(e00, e10), pack2(e01, e11));
+        }
     }
 }
 
+template <typename TS, typename R>
+cudaError_t mix_quads_t(const FilterArgs& a, cudaStream_t st) {
+    dim3 grid((unsigned)((a.W + kQuadPad + kMqX - 1) / kMqX),
+              (unsigned)((a.H + kQuadPad + kMqY - 1) / kMqY));
+    const size_t smem = mix_quads_smem(a.G, a.mix != nullptr, (int)sizeof(R));
+    auto kern = k_mix_quads<TS, R>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, kMqThreads, smem, st>>>(static_cast<const TS*>(a.S), static_cast<R*>(a.quads),
+                                         a.G, a.H, a.W, a.mix_self, a.mix_all, a.mix, a.den_f);
+    return cudaGetLastError();
+}
+
+// The density stack from the quads: rho(g, v, u) is the first value of quad (u, v).
 template <typename R>
-cudaError_t quads_t(const FilterArgs& a, cudaStream_t st) {
-    const int64_t n = (int64_t)a.G * quad_elems(a.W, a.H);
-    k_quads<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(static_cast<const R*>(a.rho),
-                                                            static_cast<R*>(a.quads), a.G, a.H,
-                                                            a.W);
+__global__ void k_rho_from_quads(const R* __restrict__ quads, R* __restrict__ rho, int G, int H,
+                                 int W) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t C = (int64_t)H * W;
+    if (idx >= (int64_t)G * C) return;
+    const int64_t g = idx / C, rem = idx % C;
+    const int v = (int)(rem / W), u = (int)(rem % W);
+    const int64_t Wq = W + kQuadPad, QC = Wq * (H + kQuadPad);
+    rho[idx] = quads[(g * QC + (int64_t)(v + 2) * Wq + (u + 2)) * 4];
+}
+
+template <typename R>
+cudaError_t rho_from_quads_t(const FilterArgs& a, cudaStream_t st) {
+    const int64_t n = (int64_t)a.G * a.H * a.W;
+    k_rho_from_quads<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        static_cast<const R*>(a.quads), static_cast<R*>(a.rho), a.G, a.H, a.W);
     return cudaGetLastError();
 }
 
@@ -394,15 +477,14 @@ template <typename TS, int STRIP>
 cudaError_t colbox_strip(const FilterArgs& a, cudaStream_t st) {
     const int nch = (a.H + kChunk - 1) / kChunk;
     if (STRIP * nch > kColThreads) return cudaErrorInvalidValue;
-    const int ntab = a.H + 2 * a.r + 2;
-    const size_t smem = (size_t)(a.H + nch) * STRIP * sizeof(TS) + (size_t)(ntab + ntab / kChunk + 1) * 4;
+    const size_t smem = colbox_smem(a.H, a.r, STRIP, sizeof(TS));
     auto kern = k_colbox<TS, STRIP>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)((a.W + STRIP - 1) / STRIP), (unsigned)a.G);
     kern<<<grid, kColThreads, smem, st>>>(static_cast<const TS*>(a.Y), static_cast<TS*>(a.S),
-                                          a.G, a.H, a.W, a.r, a.passes);
+                                          a.G, a.H, a.W, a.r, a.passes, col_halo(a.r));
     return cudaGetLastError();
 }
 
@@ -412,39 +494,6 @@ cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
     if (strip == 8) return colbox_strip<TS, 8>(a, st);
     if (strip == 4) return colbox_strip<TS, 4>(a, st);
     return colbox_strip<TS, 2>(a, st);
-}
-
-// General interaction (Eq. 3): rho_l = (sum_b num[l, b] S_b) / (den s^k), exact int64
-// numerator; the matrix is staged in shared memory once per CTA.
-template <typename TS, typename R>
-__global__ void k_combine_matrix(const TS* __restrict__ S, R* __restrict__ rho, int G, int64_t C,
-                                 const int64_t* __restrict__ num, float den) {
-    extern __shared__ long long s_num[];
-    for (int k = threadIdx.x; k < G * G; k += blockDim.x) s_num[k] = num[k];
-    __syncthreads();
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= C) return;
-    for (int l = 0; l < G; ++l) {
-        long long acc = 0;
-        for (int b = 0; b < G; ++b) acc += s_num[l * G + b] * (long long)S[(size_t)b * C + idx];
-        rho[(size_t)l * C + idx] = to_rho<R>(__fdiv_rn(__ll2float_rn(acc), den));
-    }
-}
-
-template <typename TS, typename R>
-cudaError_t combine_t(const FilterArgs& a, cudaStream_t st) {
-    if (a.mix) {
-        const int64_t C = (int64_t)a.H * a.W;
-        k_combine_matrix<TS, R><<<(unsigned)((C + 255) / 256), 256,
-                                  (size_t)a.G * a.G * sizeof(long long), st>>>(
-            static_cast<const TS*>(a.S), static_cast<R*>(a.rho), a.G, C, a.mix, a.den_f);
-        return cudaGetLastError();
-    }
-    const int64_t C = (int64_t)a.H * a.W;
-    k_combine<TS, R><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(
-        static_cast<const TS*>(a.S), static_cast<R*>(a.rho), a.G, C, a.mix_self, a.mix_all,
-        a.den_f);
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -457,10 +506,8 @@ bool rowbox_mode_valid(int mode, int W) {
 
 bool colbox_strip_valid(int strip, int H, int r, int sum_bytes) {
     const int nch = (H + kChunk - 1) / kChunk;
-    const int ntab = H + 2 * r + 2;
-    const size_t smem = (size_t)(H + nch) * strip * sum_bytes + (size_t)(ntab + ntab / kChunk + 1) * 4;
     return (strip == 2 || strip == 4 || strip == 8) && strip * nch <= kColThreads &&
-           smem <= (size_t)227 * 1024;
+           colbox_smem(H, r, strip, sum_bytes) <= (size_t)227 * 1024;
 }
 
 cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
@@ -527,28 +574,28 @@ cudaError_t launch_fold_hist(uint32_t* hist, int64_t n, int copies, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st) {
-    switch (rho_dtype) {
-        case 0: return quads_t<float>(a, st);
-        case 1: return quads_t<__nv_bfloat16>(a, st);
-        case 2: return quads_t<__half>(a, st);
+cudaError_t launch_mix_quads(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st) {
+    if (sum_bits == 32) {
+        switch (rho_dtype) {
+            case 0: return mix_quads_t<uint32_t, float>(a, st);
+            case 1: return mix_quads_t<uint32_t, __nv_bfloat16>(a, st);
+            case 2: return mix_quads_t<uint32_t, __half>(a, st);
+        }
+    } else {
+        switch (rho_dtype) {
+            case 0: return mix_quads_t<unsigned long long, float>(a, st);
+            case 1: return mix_quads_t<unsigned long long, __nv_bfloat16>(a, st);
+            case 2: return mix_quads_t<unsigned long long, __half>(a, st);
+        }
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_combine(int sum_bits, int rho_dtype, const FilterArgs& a, cudaStream_t st) {
-    if (sum_bits == 32) {
-        switch (rho_dtype) {
-            case 0: return combine_t<uint32_t, float>(a, st);
-            case 1: return combine_t<uint32_t, __nv_bfloat16>(a, st);
-            case 2: return combine_t<uint32_t, __half>(a, st);
-        }
-    } else {
-        switch (rho_dtype) {
-            case 0: return combine_t<unsigned long long, float>(a, st);
-            case 1: return combine_t<unsigned long long, __nv_bfloat16>(a, st);
-            case 2: return combine_t<unsigned long long, __half>(a, st);
-        }
+cudaError_t launch_rho_from_quads(int rho_dtype, const FilterArgs& a, cudaStream_t st) {
+    switch (rho_dtype) {
+        case 0: return rho_from_quads_t<float>(a, st);
+        case 1: return rho_from_quads_t<__nv_bfloat16>(a, st);
+        case 2: return rho_from_quads_t<__half>(a, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -11,45 +11,46 @@
 namespace heb {
 namespace {
 
-// Advection of one interior point (Eq. 5) with the optimised step (Sec. 3.3):
-// the direction is the bilinear interpolation of central differences at the
-// four surrounding cell centres on the reflection-extended map; the magnitude
-// starts at h and halves until the density is not lower than at x.
-template <typename T, int KT>
-__device__ __forceinline__ float2 advect_point(float2 p, const T* __restrict__ Q, int W, int H,
-                                               float h, float eps, int tries_rt, int fixed_step) {
-    const int tries = KT > 0 ? KT : tries_rt;
+// Direction and starting density of one interior point (Eq. 5): the direction
+// is the bilinear interpolation of central differences at the four surrounding
+// cell centres on the reflection-extended map, normalised by max(|g|, eps).
+struct Dir {
+    float dx, dy, rho0;
+};
+
+template <typename T>
+__device__ __forceinline__ Dir direction(float2 p, const T* __restrict__ Q, int W, int H,
+                                         float eps) {
     Frame f = frame_of(p.x, p.y, W, H);
     const int64_t Wq = W + kQuadPad;
     const int64_t c = (int64_t)(f.b0 + 2) * Wq + (f.a0 + 2);
-    // quads at (a0, b0-1), (a0-1, b0), (a0+1, b0), (a0, b0+1): the 12-texel stencil
-    float4 up = load_quad(Q, c - Wq), lf = load_quad(Q, c - 1);
-    float4 rt = load_quad(Q, c + 1), dn = load_quad(Q, c + Wq);
+    // quads at (a0, b0-1), (a0-1, b0), (a0+1, b0), (a0, b0+1): the 12-cell stencil
+    const float4 up = load_quad(Q, c - Wq), lf = load_quad(Q, c - 1);
+    const float4 rt = load_quad(Q, c + 1), dn = load_quad(Q, c + Wq);
     // E(a0,b0) = up.z, E(a0+1,b0) = up.w, E(a0,b0+1) = dn.x, E(a0+1,b0+1) = dn.y
-    // central differences (E(a+1) - E(a-1)) / 2, interpolated; halving commutes exactly with
-    // the interpolation (a power-of-two scaling), so it is applied once at the end
+    // central differences (E(a+1) - E(a-1)) / 2 at the four cell centres, interpolated;
+    // halving commutes exactly with the interpolation (a power-of-two scaling), so it is
+    // applied once at the end
     float gx = lerp_rn(lerp_rn(__fsub_rn(rt.x, lf.x), __fsub_rn(rt.y, lf.y), f.fu),
                        lerp_rn(__fsub_rn(rt.z, lf.z), __fsub_rn(rt.w, lf.w), f.fu), f.fv);
     float gy = lerp_rn(lerp_rn(__fsub_rn(dn.x, up.x), __fsub_rn(dn.y, up.y), f.fu),
                        lerp_rn(__fsub_rn(dn.z, up.z), __fsub_rn(dn.w, up.w), f.fu), f.fv);
     gx = __fmul_rn(gx, 0.5f);
     gy = __fmul_rn(gy, 0.5f);
-    float rho0 = lerp_rn(lerp_rn(up.z, up.w, f.fu), lerp_rn(dn.x, dn.y, f.fu), f.fv);
+    Dir d;
+    d.rho0 = lerp_rn(lerp_rn(up.z, up.w, f.fu), lerp_rn(dn.x, dn.y, f.fu), f.fv);
     // d = g / max(|g|, eps): one reciprocal square root (direction only)
     const float n2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
     const float inv = n2 > eps * eps ? rsqrtf(n2) : __frcp_rn(eps);
-    const float dx = __fmul_rn(gx, inv), dy = __fmul_rn(gy, inv);
-    if (fixed_step)  // KDEEB's step (Sec. 3.3): magnitude h whatever the density there
-        return make_float2(clamp_pos(__fmaf_rn(h, dx, p.x), W), clamp_pos(__fmaf_rn(h, dy, p.y), H));
-    float m = h;
-#pragma unroll
-    for (int t = 0; t < tries; ++t) {
-        float xn = clamp_pos(__fmaf_rn(m, dx, p.x), W);
-        float yn = clamp_pos(__fmaf_rn(m, dy, p.y), H);
-        if (density_at(Q, W, H, xn, yn) >= rho0) return make_float2(xn, yn);
-        m = __fmul_rn(m, 0.5f);
-    }
-    return p;
+    d.dx = __fmul_rn(gx, inv);
+    d.dy = __fmul_rn(gy, inv);
+    return d;
+}
+
+// The position a step of size m along (dx, dy) reaches, clamped to the drawing area.
+__device__ __forceinline__ float2 moved(float px, float py, float m, float dx, float dy, int W,
+                                        int H) {
+    return make_float2(clamp_pos(__fmaf_rn(m, dx, px), W), clamp_pos(__fmaf_rn(m, dy, py), H));
 }
 
 // Segment length (the arc length sums these; an approximate square root is enough).
@@ -78,7 +79,7 @@ __device__ __forceinline__ float warp_scan_incl(float x, int lane) {
     return x;
 }
 
-constexpr int kWarps = kStepThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
 
 // Segment histogram (Eq. 1 as rasterised in Sec. 4): the cells from the cell of A to
 // the cell of B by the integer Bresenham line algorithm, each gaining w (the first
@@ -114,9 +115,9 @@ __device__ __forceinline__ int raster_segment(uint32_t* hl, int W, int H, float2
 
 // Write one resampled point and splat it: it adds its edge weight to its group's cell
 // (Eq. 1, Eq. 3) in one of the histogram copies.
-__device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at, float2 R,
+__device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, float2* dst, float2 R,
                                      int w) {
-    a.pts_out[at] = R;
+    *dst = R;
     if (w != 0 && !a.seg_hist) {
         const int cx = min(max(__float2int_rd(R.x), 0), a.W - 1);
         const int cy = min(max(__float2int_rd(R.y), 0), a.H - 1);
@@ -124,99 +125,126 @@ __device__ __forceinline__ void emit(const StepArgs& a, uint32_t* hl, int64_t at
     }
 }
 
-// One block of eb slots per CTA, staged through shared memory in
-// batches of whole polylines:
-//  1. load the batch's points (coalesced), map each point to its polyline;
-//  2. advection, one thread per point, in place (a point reads only itself);
-//  3. one warp per polyline, two consecutive points per lane: Laplacian
-//     smoothing (Jacobi), then the arc lengths by a warp scan;
-//  4. new point counts (one thread per polyline) and their offsets (block
-//     scan), then one warp per polyline writes its uniformly re-spaced points,
-//     two per lane, and splats them.
-// step_block is the work of CTA bx of one graph (a); k_step runs one graph,
-// k_step_batch the CTAs of many graphs in one launch.
-template <int MODE, typename T>
-__device__ __forceinline__ void step_block(const StepArgs& a, int bx) {
-    __shared__ int s_cnt[kEdgesPerBlock];
-    __shared__ int s_loc[kEdgesPerBlock + 1];
-    __shared__ int s_grp[kEdgesPerBlock];
-    __shared__ int s_w[kEdgesPerBlock];
-    __shared__ int s_nn[kEdgesPerBlock];
-    __shared__ int s_locn[kEdgesPerBlock + 1];
-    __shared__ float s_sp[kEdgesPerBlock];
-    __shared__ int s_wtot[32];
-    __shared__ float2 s_pts[kBatchPoints];
-    __shared__ float s_cum[kBatchPoints];
-    __shared__ unsigned char s_pe[kBatchPoints];
+// Shared staging of one warp: a sub-batch of whole polylines of its block, and the
+// per-slot values the warp reads uniformly (one vector load instead of a shuffle each).
+struct StepSmem {
+    float2 pts[kStage];               // the sub-batch's points
+    float cum[kStage];                // arc lengths
+    int4 meta[kMaxEdgesPerWarp];      // per slot: first point in the region, count, group, weight
+    int4 outm[kMaxEdgesPerWarp];      // per slot of the sub-batch: new count, its first output,
+                                      // spacing (float bits)
+    unsigned char pe[kStage];         // slot (within the block) of each staged point
+};
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t e0 = (int64_t)bx * a.eb;
+// Advection of the staged interior points (Eq. 5, Sec. 3.3), one thread per point:
+// the direction, then step trials of size h, h/2, ... until the density at the
+// moved position is not lower than at the point (none accepted: the point stays).
+template <typename T>
+__device__ __forceinline__ void advect_staged(const StepArgs& a, StepSmem& S, int np, int p0,
+                                              const T* quads, int64_t QC4, float h) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < np; c += 32) {
+        const int k = c + lane;
+        const int4 md = S.meta[k < np ? S.pe[k] : 0];
+        const int q = md.x - p0, n = md.y, g = md.z;
+        const int j = k - q;
+        if (k < np && j > 0 && j < n - 1) {
+            const T* Q = quads + (int64_t)g * QC4;
+            const float2 p = S.pts[k];
+            const Dir d = direction(p, Q, a.W, a.H, a.eps);
+            if (a.fixed_step) {  // KDEEB's step (Sec. 3.3): h whatever the density there
+                S.pts[k] = moved(p.x, p.y, h, d.dx, d.dy, a.W, a.H);
+                continue;
+            }
+            float m = h;
+            for (int t = 0; t < a.tries; ++t) {
+                const float2 x1 = moved(p.x, p.y, m, d.dx, d.dy, a.W, a.H);
+                if (density_at(Q, a.W, a.H, x1.x, x1.y) >= d.rho0) {
+                    S.pts[k] = x1;
+                    break;
+                }
+                m = __fmul_rn(m, 0.5f);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// The work of one warp on its block of eb slots (blk: the block's index in the
+// layout). The warp stages sub-batches of whole polylines in its own shared
+// memory and works through them alone, with warp-level synchronisation only:
+//  1. load the sub-batch's points (coalesced) and tag each with its slot;
+//  2. advection, one thread per point, in place (a point reads only itself);
+//  3. per polyline, two consecutive points per lane: Laplacian smoothing
+//     (Jacobi), then the arc lengths by a warp scan;
+//  4. new point counts and spacings (one lane per polyline) and their offsets
+//     (a warp scan); then per polyline the uniformly re-spaced points, two per
+//     lane, written out and splatted.
+template <int MODE, typename T>
+__device__ __forceinline__ void step_warp(const StepArgs& a, int64_t blk, StepSmem& S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = blk * a.eb;
+    if (e0 >= a.E) return;
     const int nb = (int)min((int64_t)a.eb, a.E - e0);
-    const int64_t region = (int64_t)bx * a.eb * a.cap;
-    const int64_t QC = quad_elems(a.W, a.H);
-    const size_t hist_copy = bx % kHistCopies;
+    const int64_t region = blk * a.eb * (int64_t)a.cap;
+    const float2* __restrict__ pin = a.pts_in + region;
+    float2* __restrict__ pout = a.pts_out + region;
+    const int64_t QC4 = quad_elems(a.W, a.H) * 4;
+    const T* quads = static_cast<const T*>(a.quads);
+    uint32_t* hist = a.hist + (size_t)(blk % kHistCopies) * a.G * (size_t)a.W * a.H;
     const float h = a.h_sched ? __ldg(a.h_sched + __ldg(a.iter)) : a.h;
 
-    for (int i = tid; i < nb; i += kStepThreads) {
-        s_cnt[i] = a.cnt_in[e0 + i];
-        s_grp[i] = a.group[e0 + i];
-        s_w[i] = a.weight[e0 + i];
+    // lane i holds slot e0 + i: its point count, group, weight and, after the scan, the
+    // offset of its first point in the block's region
+    int cnt = 0, grp = 0, wgt = 0;
+    if (lane < nb) {
+        cnt = a.cnt_in[e0 + lane];
+        grp = a.group[e0 + lane];
+        wgt = a.weight[e0 + lane];
     }
-    __syncthreads();
-    block_scan_excl(s_cnt, s_loc, nb, s_wtot);
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int loc = inc - cnt;
+    if (lane < nb) S.meta[lane] = make_int4(loc, cnt, grp, wgt);
+    __syncwarp();
 
     int out_base = 0;
     for (int b0 = 0; b0 < nb;) {
-        // the longest run of whole polylines that fits the staging buffer
-        int b1;
-        {
-            int lim = s_loc[b0] + kBatchPoints, lo = b0 + 1, hi = nb;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_loc[mid] <= lim) lo = mid; else hi = mid - 1;
-            }
-            b1 = lo;
-        }
-        const int p0 = s_loc[b0];
-        const int np = s_loc[b1] - p0;
-        for (int k = tid; k < np; k += kStepThreads) s_pts[k] = a.pts_in[region + p0 + k];
+        // polylines [b0, b1): the longest run from b0 that fits the staging buffer
+        const int p0 = __shfl_sync(kFull, loc, b0);
+        const int b1 =
+            b0 + __popc(__ballot_sync(kFull, lane >= b0 && lane < nb && inc - p0 <= kStage));
+        const int np = __shfl_sync(kFull, inc, b1 - 1) - p0;
+        for (int k = lane; k < np; k += 32) S.pts[k] = pin[p0 + k];
         if (MODE & kModeAdvect) {
-            for (int i = b0 + warp; i < b1; i += kWarps) {
-                const int q = s_loc[i] - p0, n = s_cnt[i];
-                for (int j = lane; j < n; j += 32) s_pe[q + j] = (unsigned char)(i - b0);
+            for (int i = b0; i < b1; ++i) {
+                const int4 md = S.meta[i];
+                for (int j = lane; j < md.y; j += 32) S.pe[md.x - p0 + j] = (unsigned char)i;
             }
         }
-        __syncthreads();
+        __syncwarp();
 
-        if (MODE & kModeAdvect) {
-            for (int k = tid; k < np; k += kStepThreads) {
-                const int i = b0 + s_pe[k];
-                const int j = p0 + k - s_loc[i];
-                if (j > 0 && j < s_cnt[i] - 1) {
-                    const T* Q = static_cast<const T*>(a.quads) + (int64_t)s_grp[i] * QC * 4;
-                    s_pts[k] = a.tries == 8
-                                   ? advect_point<T, 8>(s_pts[k], Q, a.W, a.H, h, a.eps, 8, a.fixed_step)
-                                   : advect_point<T, 0>(s_pts[k], Q, a.W, a.H, h, a.eps, a.tries,
-                                                        a.fixed_step);
-                }
-            }
-            __syncthreads();
-        }
+        if (MODE & kModeAdvect) advect_staged<T>(a, S, np, p0, quads, QC4, h);
 
-        // one warp per polyline, two consecutive points per lane (j = 2 lane, 2 lane + 1;
+        // one polyline at a time, two consecutive points per lane (j = 2 lane, 2 lane + 1;
         // a polyline has at most 64 points): Laplacian smoothing, then the arc lengths. The
         // neighbours across lanes come by shuffles, so a lane writes only its own points.
-        for (int i = b0 + warp; i < b1; i += kWarps) {
-            const int q = s_loc[i] - p0, n = s_cnt[i];
+        for (int i = b0; i < b1; ++i) {
+            const int4 md = S.meta[i];
+            const int q = md.x - p0, n = md.y;
             const int j0 = 2 * lane, j1 = j0 + 1;
-            float2 A0 = j0 < n ? s_pts[q + j0] : make_float2(0.0f, 0.0f);
-            float2 A1 = j1 < n ? s_pts[q + j1] : make_float2(0.0f, 0.0f);
+            float2 A0 = j0 < n ? S.pts[q + j0] : make_float2(0.0f, 0.0f);
+            float2 A1 = j1 < n ? S.pts[q + j1] : make_float2(0.0f, 0.0f);
             if (MODE & kModeAdvect) {
                 // point j0 - 1 is the previous lane's second, j1 + 1 the next lane's first
-                const float lx = __shfl_up_sync(0xffffffffu, A1.x, 1);
-                const float ly = __shfl_up_sync(0xffffffffu, A1.y, 1);
-                const float rx = __shfl_down_sync(0xffffffffu, A0.x, 1);
-                const float ry = __shfl_down_sync(0xffffffffu, A0.y, 1);
+                const float lx = __shfl_up_sync(kFull, A1.x, 1);
+                const float ly = __shfl_up_sync(kFull, A1.y, 1);
+                const float rx = __shfl_down_sync(kFull, A0.x, 1);
+                const float ry = __shfl_down_sync(kFull, A0.y, 1);
                 float2 B0 = A0, B1 = A1;
                 if (j0 > 0 && j0 < n - 1) {
                     B0.x = __fmaf_rn(a.lap_half_beta, __fadd_rn(lx, A1.x), __fmul_rn(a.lap_keep, A0.x));
@@ -228,52 +256,61 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx) {
                 }
                 A0 = B0;
                 A1 = B1;
-                if (j0 < n) s_pts[q + j0] = A0;
-                if (j1 < n) s_pts[q + j1] = A1;
-                if (!(MODE & kModeResample)) {
-                    if (j0 < n) a.pts_out[region + p0 + q + j0] = A0;
-                    if (j1 < n) a.pts_out[region + p0 + q + j1] = A1;
+                if (MODE & kModeResample) {
+                    if (j0 < n) S.pts[q + j0] = A0;
+                    if (j1 < n) S.pts[q + j1] = A1;
+                } else {
+                    if (j0 < n) pout[p0 + q + j0] = A0;
+                    if (j1 < n) pout[p0 + q + j1] = A1;
                     if (lane == 0) a.cnt_out[e0 + i] = n;
                 }
             }
             if (MODE & kModeResample) {
                 // cum[j]: lengths of the segments up to point j, by a warp scan of the lanes'
                 // pair sums
-                const float px = __shfl_up_sync(0xffffffffu, A1.x, 1);
-                const float py = __shfl_up_sync(0xffffffffu, A1.y, 1);
+                const float px = __shfl_up_sync(kFull, A1.x, 1);
+                const float py = __shfl_up_sync(kFull, A1.y, 1);
                 const float s0 = (j0 >= 1 && j0 < n) ? seg_len(make_float2(px, py), A0) : 0.0f;
                 const float s1 = j1 < n ? seg_len(A0, A1) : 0.0f;
                 const float incl = warp_scan_incl(__fadd_rn(s0, s1), lane);
-                float ex = __shfl_up_sync(0xffffffffu, incl, 1);
+                float ex = __shfl_up_sync(kFull, incl, 1);
                 if (lane == 0) ex = 0.0f;
                 const float c0 = __fadd_rn(ex, s0);
-                if (j0 < n) s_cum[q + j0] = c0;
-                if (j1 < n) s_cum[q + j1] = __fadd_rn(c0, s1);
+                if (j0 < n) S.cum[q + j0] = c0;
+                if (j1 < n) S.cum[q + j1] = __fadd_rn(c0, s1);
             }
         }
-        __syncthreads();
+        __syncwarp();
 
         if (MODE & kModeResample) {
-            // new point counts and spacings, one thread per polyline (the same thread then
-            // reads its count first in the block scan)
-            for (int i = b0 + tid; i < b1; i += kStepThreads) {
-                const float L = s_cum[s_loc[i] - p0 + s_cnt[i] - 1];
-                const int m = new_count(L, a);
-                s_nn[i] = m;
-                s_sp[i] = __fdiv_rn(L, (float)(m - 1));
+            // new point count and spacing of polyline `lane`, and its first output offset
+            int mc = 0;
+            float sp = 0.0f;
+            if (lane >= b0 && lane < b1) {
+                const float L = S.cum[loc - p0 + cnt - 1];
+                mc = new_count(L, a);
+                sp = __fdiv_rn(L, (float)(mc - 1));
             }
-            block_scan_excl(s_nn + b0, s_locn + b0, b1 - b0, s_wtot);
-            for (int i = b0 + warp; i < b1; i += kWarps) {
-                const int q = s_loc[i] - p0, n = s_cnt[i], m = s_nn[i];
-                const float sp = s_sp[i];
-                const float L = s_cum[q + n - 1];
-                const int64_t ob = region + out_base + s_locn[i];
-                const int g = s_grp[i], w = s_w[i];
-                uint32_t* hl = a.hist + hist_copy * a.G * (size_t)a.W * a.H + (size_t)g * a.W * a.H;
+            int minc = mc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, minc, o);
+                if (lane >= o) minc += y;
+            }
+            if (lane >= b0 && lane < b1)
+                S.outm[lane] = make_int4(mc, out_base + minc - mc, __float_as_int(sp), 0);
+            __syncwarp();
+            for (int i = b0; i < b1; ++i) {
+                const int4 md = S.meta[i], mo = S.outm[i];
+                const int q = md.x - p0, n = md.y, g = md.z, w = md.w;
+                const int m = mo.x, ob = mo.y;
+                const float spi = __int_as_float(mo.z);
+                const float L = S.cum[q + n - 1];
+                uint32_t* hl = hist + (size_t)g * a.W * a.H;
                 // directed graphs (Sec. 3): interior points shift along the edge normal
                 float ox = 0.0f, oy = 0.0f;
                 if (a.dir_amount != 0.0f) {
-                    const float2 P0 = s_pts[q], P1 = s_pts[q + n - 1];
+                    const float2 P0 = S.pts[q], P1 = S.pts[q + n - 1];
                     const float ddx = __fsub_rn(P1.x, P0.x), ddy = __fsub_rn(P1.y, P0.y);
                     const float len = sqrtf(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)));
                     if (len > 0.0f) {
@@ -293,71 +330,76 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx) {
                     if (j >= m) break;
                     float2 R;
                     if (j == m - 1) {
-                        R = s_pts[q + n - 1];
+                        R = S.pts[q + n - 1];
                     } else if (j == 0 || L == 0.0f) {
-                        R = s_pts[q];
+                        R = S.pts[q];
                     } else {
-                        const float t = __fmul_rn((float)j, sp);
+                        const float t = __fmul_rn((float)j, spi);
                         if (h2 == 0) {
                             int pos = 0;  // the last k in [0, n-2] with cum[k] <= t
 #pragma unroll
                             for (int step = 32; step > 0; step >>= 1) {
                                 const int c = pos + step;
-                                if (c <= n - 2 && !(s_cum[q + c] > t)) pos = c;
+                                if (c <= n - 2 && !(S.cum[q + c] > t)) pos = c;
                             }
                             lo = pos + 1;
                         } else {
-                            while (lo < n - 1 && !(s_cum[q + lo] > t)) ++lo;
+                            while (lo < n - 1 && !(S.cum[q + lo] > t)) ++lo;
                         }
-                        const float c0 = s_cum[q + lo - 1];
-                        const float seg = __fsub_rn(s_cum[q + lo], c0);
+                        const float c0 = S.cum[q + lo - 1];
+                        const float seg = __fsub_rn(S.cum[q + lo], c0);
                         float fr = seg > 0.0f ? __fdividef(__fsub_rn(t, c0), seg) : 0.0f;
                         fr = fminf(fmaxf(fr, 0.0f), 1.0f);
-                        const float2 A = s_pts[q + lo - 1], B = s_pts[q + lo];
+                        const float2 A = S.pts[q + lo - 1], B = S.pts[q + lo];
                         R = make_float2(lerp_rn(A.x, B.x, fr), lerp_rn(A.y, B.y, fr));
                         if (ox != 0.0f || oy != 0.0f)
                             R = make_float2(clamp_pos(__fadd_rn(R.x, ox), a.W),
                                             clamp_pos(__fadd_rn(R.y, oy), a.H));
                     }
-                    emit(a, hl, ob + j, R, w);
+                    emit(a, hl, pout + ob + j, R, w);
                 }
                 if (a.seg_hist && w != 0) {
                     // segments of the new polyline (its points were written by this warp)
                     __syncwarp();
                     unsigned long long cells = 0;
                     for (int j = 1 + lane; j < m; j += 32)
-                        cells += raster_segment(hl, a.W, a.H, a.pts_out[ob + j - 1],
-                                                a.pts_out[ob + j], j >= 2, (unsigned)w);
+                        cells += raster_segment(hl, a.W, a.H, pout[ob + j - 1], pout[ob + j],
+                                                j >= 2, (unsigned)w);
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(0xffffffffu, cells, o);
+                    for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(kFull, cells, o);
                     if (lane == 0 && a.mass) atomicAdd(a.mass, cells * (unsigned long long)w);
                 }
                 if (lane == 0) a.cnt_out[e0 + i] = m;
             }
-            if (tid == 0 && a.n_splat)
-                atomicAdd(a.n_splat, (unsigned long long)s_locn[b1]);
-            out_base += s_locn[b1];
-            __syncthreads();
+            out_base += __shfl_sync(kFull, minc, 31);
         }
+        __syncwarp();  // the next sub-batch overwrites the staging
         b0 = b1;
     }
+    if ((MODE & kModeResample) && lane == 0 && a.n_splat)
+        atomicAdd(a.n_splat, (unsigned long long)out_base);
 }
 
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kStepThreads) k_step(const __grid_constant__ StepArgs a) {
-    step_block<MODE, T>(a, blockIdx.x);
+__global__ void __launch_bounds__(kStepThreads, 8) k_step(const __grid_constant__ StepArgs a) {
+    __shared__ StepSmem smem[kStepWarps];
+    const int warp = threadIdx.x >> 5;
+    step_warp<MODE, T>(a, (int64_t)blockIdx.x * kStepWarps + warp, smem[warp]);
 }
 
 // Many graphs in one launch: CTA blockIdx.x belongs to graph m with
 // blk[m] <= blockIdx.x < blk[m + 1] and is that graph's CTA blockIdx.x - blk[m].
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kStepThreads, 6) k_step_batch(const __grid_constant__ BatchStepArgs P) {
+__global__ void __launch_bounds__(kStepThreads, 8) k_step_batch(const __grid_constant__ BatchStepArgs P) {
+    __shared__ StepSmem smem[kStepWarps];
     int lo = 0, hi = P.n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (P.blk[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
-    step_block<MODE, T>(P.a[lo], (int)blockIdx.x - P.blk[lo]);
+    const int warp = threadIdx.x >> 5;
+    step_warp<MODE, T>(P.a[lo], (int64_t)((int)blockIdx.x - P.blk[lo]) * kStepWarps + warp,
+                       smem[warp]);
 }
 
 __global__ void k_advance_batch(const __grid_constant__ BatchStepArgs P) {
@@ -369,6 +411,8 @@ template <typename T>
 cudaError_t launch_step_batch_t(int mode, const BatchStepArgs& P, cudaStream_t st) {
     const int total = P.blk[P.n];
     if (total <= 0) return cudaSuccess;
+    for (int m = 0; m < P.n; ++m)
+        if (P.a[m].eb < 1 || P.a[m].eb > kMaxEdgesPerWarp) return cudaErrorInvalidValue;
     switch (mode) {
         case kModeResample: k_step_batch<kModeResample, T><<<total, kStepThreads, 0, st>>>(P); break;
         case kModeAdvect: k_step_batch<kModeAdvect, T><<<total, kStepThreads, 0, st>>>(P); break;
@@ -383,8 +427,8 @@ cudaError_t launch_step_batch_t(int mode, const BatchStepArgs& P, cudaStream_t s
 template <typename T>
 cudaError_t launch_step_t(int mode, const StepArgs& a, cudaStream_t st) {
     if (a.E <= 0) return cudaSuccess;
-    if (a.eb < 1 || a.eb > kEdgesPerBlock) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((a.E + a.eb - 1) / a.eb));
+    if (a.eb < 1 || a.eb > kMaxEdgesPerWarp) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)step_ctas(a.E, a.eb));
     switch (mode) {
         case kModeResample: k_step<kModeResample, T><<<grid, kStepThreads, 0, st>>>(a); break;
         case kModeAdvect: k_step<kModeAdvect, T><<<grid, kStepThreads, 0, st>>>(a); break;
