@@ -106,7 +106,7 @@ typedef struct {
                                    over iterations of the points each iteration advects */
     int32_t tile_eb;            /* edges per block of the point kernels */
     int32_t tile_row;           /* row-pass variant: 0 by width, 1 register rows, 2 shared rows */
-    int32_t tile_strip;         /* column-pass strip: 0 by height, else 2, 4 or 8 columns */
+    int32_t tile_strip;         /* column-pass strip: 0 by shape, else 16 (TMA), 8, 4 or 2 */
     int32_t reserved;
 } bundle_info;
 
@@ -305,9 +305,11 @@ bundle_status bundle_autotune(bundle_ctx* ctx);
  * shape): eb 0 (keep) or 4, 8, 16, 32 edges per warp-owned block of the point
  * layout -- only on a fresh bundle_init context;
  * row_mode 0 (by width), 1 (register rows, widths of 225..256, 481..512 or 993..1024
- * cells), 2 (shared-memory rows); col_strip 0 (by height), 2, 4 or 8 (when the strip's
- * column fits in shared memory). EINVAL for a choice that does not exist, ESTATE for
- * eb on an iterated context or for batches. */
+ * cells), 2 (shared-memory rows); col_strip 0 (by shape), 16 (strips staged by the
+ * tensor memory accelerator: heights up to 1024, width x sum bytes a multiple of 16),
+ * 2, 4 or 8 (strips copied with cp.async, when the strip's column fits in shared
+ * memory; 8 is the default up to height 1024). EINVAL for a choice that does not exist,
+ * ESTATE for eb on an iterated context or for batches. */
 bundle_status bundle_set_tiles(bundle_ctx* ctx, int32_t eb, int32_t row_mode, int32_t col_strip);
 
 /* Sizes, widths, map, schedule and point counts of a context (synchronises the stream).

@@ -598,6 +598,7 @@ FilterArgs filter_args(bundle_ctx* c) {
     f.den_f = c->den_f;
     f.strip = c->col_strip;
     f.row_mode = c->row_mode;
+    f.err_flag = c->d_flag;
     return f;
 }
 
@@ -1328,8 +1329,8 @@ static bundle_status tune_filter(bundle_ctx* c) {
             }
         }
     }
-    for (int strip = 2; strip <= 8; strip *= 2) {
-        if (!colbox_strip_valid(strip, c->H, c->p.radius, sb)) continue;
+    for (int strip = 2; strip <= 16; strip *= 2) {
+        if (!colbox_strip_valid(strip, c->W, c->H, c->p.radius, sb)) continue;
         f.strip = strip;
         for (int rep = 0; rep < 3; ++rep) {
             float ms = 0;
@@ -1460,7 +1461,7 @@ bundle_status bundle_set_tiles(bundle_ctx* c, int32_t eb, int32_t row_mode, int3
     if (!rowbox_mode_valid(row_mode, c->W))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: row variant %d does not exist for "
                     "width %d", row_mode, c->W);
-    if (col_strip != 0 && !colbox_strip_valid(col_strip, c->H, c->p.radius, c->sum_bits / 8))
+    if (col_strip != 0 && !colbox_strip_valid(col_strip, c->W, c->H, c->p.radius, c->sum_bits / 8))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: strip %d does not fit height %d",
                     col_strip, c->H);
     if (eb != 0 && eb != c->eb) {
@@ -1507,6 +1508,9 @@ static bundle_status check_device_flag(bundle_ctx* c) {
     int32_t f = 0;
     CUDA_TRY(&c->err, cudaMemcpyAsync(&f, c->d_flag, sizeof f, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(&c->err, cudaStreamSynchronize(c->stream));
+    if (f == 2)
+        return fail(&c->err, BUNDLE_ETIMEOUT,
+                    "a tensor-memory copy of the column pass did not complete in time");
     if (f)
         return fail(&c->err, BUNDLE_EOVERFLOW,
                     "segment histogram mass exceeded %llu: the int64 smoothed sums could wrap",

@@ -9,6 +9,8 @@
 // memory. Each 1D pass is the difference form of a 1D integral image kept as a
 // running window sum. All sums are unsigned integers: modular wrap-around
 // cancels exactly, so every box sum that fits its type is exact.
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime)
+
 #include "internal.cuh"
 
 namespace heb {
@@ -316,6 +318,124 @@ __global__ void __launch_bounds__(kColThreads)
     }
 }
 
+// --------------------------------------------- column passes, TMA-staged strips
+// The same passes on strips of 16 columns staged by the tensor memory accelerator:
+// one thread issues a 2D box copy (16 columns x 16 rows) per chunk of the strip, the
+// CTA waits for the bytes on an mbarrier. A row of the strip is 16 columns wide (128 B
+// for 64-bit sums), so a warp -- 16 columns of 2 chunks -- reads one row of each chunk
+// without bank conflicts, and the rows need no padding (every box lands 128-byte
+// aligned). 1024 threads cover 64 chunks: heights up to 1024.
+constexpr int kTmaStrip = 16;
+constexpr int kTmaThreads = kTmaStrip * 64;
+constexpr unsigned kTmaWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Wait (bounded) for phase `parity` of the mbarrier at shared address `bar`.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+inline int tma_halo(int r) { return (r + 1 + kChunk - 1) / kChunk * kChunk; }
+inline size_t colbox_tma_smem(int H, int r, int sum_bytes) {
+    // the strip with its border rows, 128 bytes of alignment slack, the mbarrier
+    return (size_t)(H + 2 * tma_halo(r)) * kTmaStrip * sum_bytes + 128 + 16;
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kTmaThreads)
+    k_colbox_tma(const __grid_constant__ CUtensorMap ymap, TS* __restrict__ S, int G, int H,
+                 int W, int r, int passes, int halo, int32_t* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    TS* buf = reinterpret_cast<TS*>(base);  // row t (t in [-halo, H + halo)): buf[(halo + t) * 16]
+    const int rows = H + 2 * halo;
+    const uint32_t bar = smem_u32(base + (size_t)rows * kTmaStrip * sizeof(TS));
+    const int g = blockIdx.y, x0 = blockIdx.x * kTmaStrip;
+    const int j = threadIdx.x % kTmaStrip, ch = threadIdx.x / kTmaStrip;
+    const int nch = (H + kChunk - 1) / kChunk;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // every box is counted whole, rows past the height included (they arrive zero-filled
+        // and land in the border, which is rewritten below)
+        const uint32_t bytes = (uint32_t)(nch * kChunk * kTmaStrip * sizeof(TS));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                     : "memory");
+        for (int c = 0; c < nch; ++c) {
+            const uint32_t dst = smem_u32(buf + (size_t)(halo + kChunk * c) * kTmaStrip);
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+                "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(x0), "r"(kChunk * c), "r"(g), "r"(bar)
+                : "memory");
+        }
+    }
+    const bool ok = mbar_wait(bar, 0, kTmaWaitLimit);
+    if (__syncthreads_or(!ok)) {
+        // the copies did not land in time: report it, let any copy still in flight finish
+        // (bounded again) before the CTA's shared memory is released, leave S untouched
+        if (threadIdx.x == 0 && err) atomicExch(err, 2);
+        mbar_wait(bar, 0, kTmaWaitLimit);
+        return;
+    }
+    auto refresh_border = [&]() {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * (r + 1) * kTmaStrip; k += blockDim.x) {
+            const int e = k / kTmaStrip, c = k % kTmaStrip;
+            const int t = e <= r ? -1 - e : H + (e - r - 1);
+            buf[(size_t)(halo + t) * kTmaStrip + c] =
+                buf[(size_t)(halo + reflect_index(t, H)) * kTmaStrip + c];
+        }
+        __syncthreads();
+    };
+    refresh_border();
+    const int i0 = ch * kChunk;
+    const int len = max(0, min(kChunk, H - i0));
+    TS* col = buf + (size_t)(halo + i0) * kTmaStrip + j;  // row i0 + x: col[x * 16]
+    TS out[kChunk];
+    for (int p = 0; p < passes; ++p) {
+        if (len > 0) {
+            TS s = 0;
+            for (int x = -1 - r; x <= -1 + r; ++x) s += col[x * kTmaStrip];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                if (q < len) {
+                    s += col[(q + r) * kTmaStrip] - col[(q - r - 1) * kTmaStrip];
+                    out[q] = s;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+            if (q < len) col[q * kTmaStrip] = out[q];
+        refresh_border();
+    }
+    const size_t lay = (size_t)g * H * W;
+    for (int idx = threadIdx.x; idx < H * kTmaStrip; idx += blockDim.x) {
+        const int row = idx / kTmaStrip, c = idx % kTmaStrip, x = x0 + c;
+        if (x < W) S[lay + (size_t)row * W + x] = buf[(size_t)(halo + row) * kTmaStrip + c];
+    }
+}
+
 // -------------------------------------------------------------- layer mixing
 // Eq. 3 / Eq. 4 after smoothing: with alpha = p / q and B groups,
 //   rho_l = (S_l - alpha / (B - 1) * sum_{b != l} S_b) / s^k
@@ -488,9 +608,68 @@ cudaError_t colbox_strip(const FilterArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The driver's tensor-map encoder, fetched through the runtime once (null if unavailable).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder() {
+    static const EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Whether the TMA-staged strip applies: heights up to 1024 (64 chunks of 16 rows per CTA),
+// rows of the tensor a multiple of 16 bytes, the strip in shared memory, an encoder.
+bool colbox_tma_fits(int W, int H, int r, int sum_bytes) {
+    return H >= 1 && H <= 64 * kChunk && ((size_t)W * sum_bytes) % 16 == 0 &&
+           colbox_tma_smem(H, r, sum_bytes) <= (size_t)227 * 1024 && tensor_map_encoder();
+}
+
+template <typename TS>
+cudaError_t colbox_tma_t(const FilterArgs& a, cudaStream_t st) {
+    if (!colbox_tma_fits(a.W, a.H, a.r, (int)sizeof(TS)) || (reinterpret_cast<uintptr_t>(a.Y) & 15))
+        return cudaErrorInvalidValue;
+    // [G][H][W] of the sum type; boxes of 16 columns x 16 rows x 1 layer; columns past W and
+    // rows past H arrive as zeros
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.G};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.W * sizeof(TS),
+                                   (cuuint64_t)a.W * a.H * sizeof(TS)};
+    const cuuint32_t box[3] = {(cuuint32_t)kTmaStrip, (cuuint32_t)kChunk, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult cr = tensor_map_encoder()(
+        &map, sizeof(TS) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3u,
+        const_cast<void*>(a.Y), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const size_t smem = colbox_tma_smem(a.H, a.r, sizeof(TS));
+    auto kern = k_colbox_tma<TS>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)((a.W + kTmaStrip - 1) / kTmaStrip), (unsigned)a.G);
+    kern<<<grid, kTmaThreads, smem, st>>>(map, static_cast<TS*>(a.S), a.G, a.H, a.W, a.r,
+                                          a.passes, tma_halo(a.r), a.err_flag);
+    return cudaGetLastError();
+}
+
+// Strip 16 is the TMA-staged pass, 8, 4 and 2 the strips copied by cp.async. By default
+// the 8-column strip: two of its CTAs share an SM and overlap one's copy with the other's
+// passes, where the TMA strip's one 1024-thread CTA per SM cannot (61 vs 71 us at
+// 8 x 1024^2, int64); the autotuner may still pick the TMA strip for a graph.
 template <typename TS>
 cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
     const int strip = a.strip ? a.strip : (a.H <= 1024 ? 8 : a.H <= 2048 ? 4 : 2);
+    if (strip == kTmaStrip) return colbox_tma_t<TS>(a, st);
     if (strip == 8) return colbox_strip<TS, 8>(a, st);
     if (strip == 4) return colbox_strip<TS, 4>(a, st);
     return colbox_strip<TS, 2>(a, st);
@@ -504,7 +683,8 @@ bool rowbox_mode_valid(int mode, int W) {
     return mode == 0 || mode == 2;
 }
 
-bool colbox_strip_valid(int strip, int H, int r, int sum_bytes) {
+bool colbox_strip_valid(int strip, int W, int H, int r, int sum_bytes) {
+    if (strip == kTmaStrip) return colbox_tma_fits(W, H, r, sum_bytes);
     const int nch = (H + kChunk - 1) / kChunk;
     return (strip == 2 || strip == 4 || strip == 8) && strip * nch <= kColThreads &&
            colbox_smem(H, r, strip, sum_bytes) <= (size_t)227 * 1024;
