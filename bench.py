@@ -173,19 +173,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kind, workload_name, algorithmic):
-    """DRAM bytes per launch from the committed ncu capture, if the kernels are unchanged:
-    the captured launches' DRAM bytes per algorithmic byte, times this run's algorithmic
-    bytes per launch (the capture's launches process a different number of points than the
-    timed average; traffic grows in proportion to them)."""
-    path = os.path.join(ROOT, "profiles", "k_step_traffic_lattice-5M-8groups.md")
+def measured_traffic(kind, algorithmic):
+    """DRAM bytes per launch from the committed ncu capture, if the step kernel is unchanged:
+    the captured launch's DRAM bytes per algorithmic byte, times this run's algorithmic bytes
+    per launch. The capture is taken on the 1M-edge lattice case (same 8 x 1024^2 stack) and
+    scaled to a full launch by the points it processes: traffic grows in proportion to them."""
+    path = os.path.join(ROOT, "profiles", "k_step_lattice-1M-8groups.md")
     try:
         with open(path) as fh:
             text = fh.read()
         d = json.loads(text.split("```json", 1)[1].split("```", 1)[0])
     except Exception:
         return None
-    ent = d.get(workload_name, {}).get(kind)
+    ent = d.get(kind)
     if not ent or ent.get("source_hash") != kernel_source_hash():
         return None
     return ent["dram_bytes_per_launch"] / ent["algorithmic_bytes_per_launch"] * algorithmic
@@ -469,7 +469,7 @@ def run_ours(args):
     dom_bytes = algorithmic_bytes(dom, N_prof, E, GC, b_sum, b_rho, MC)
     peak, peak_src = peaks()
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = measured_traffic(dom, w.name, dom_bytes)
+    traffic = measured_traffic(dom, dom_bytes)
     per_kernel = {}
     for k, (tms, n) in kern.items():
         b = algorithmic_bytes(k, N_prof, E, GC, b_sum, b_rho, MC)
