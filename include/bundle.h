@@ -105,7 +105,8 @@ typedef struct {
     int64_t points_processed;   /* sample points resampled and splatted since init: the sum
                                    over iterations of the points each iteration advects */
     int32_t tile_eb;            /* edges per block of the point kernels */
-    int32_t tile_row;           /* row-pass variant: 0 by width, 1 register rows, 2 shared rows */
+    int32_t tile_row;           /* row-pass variant: 0 by shape, 1 register rows, 2 shared rows,
+                                   3 register windows with shuffled borders */
     int32_t tile_strip;         /* column-pass strip: 0 by shape, else 16 (TMA), 8, 4 or 2 */
     int32_t reserved;
 } bundle_info;
@@ -304,8 +305,10 @@ bundle_status bundle_autotune(bundle_ctx* ctx);
 /* Set the tiles by hand (e.g. those an earlier bundle_autotune chose for the same
  * shape): eb 0 (keep) or 4, 8, 16, 32 edges per warp-owned block of the point
  * layout -- only on a fresh bundle_init context;
- * row_mode 0 (by width), 1 (register rows, widths of 225..256, 481..512 or 993..1024
- * cells), 2 (shared-memory rows); col_strip 0 (by shape), 16 (strips staged by the
+ * row_mode 0 (by shape), 1 (register rows, widths of 225..256, 481..512 or 993..1024
+ * cells), 2 (shared-memory rows), 3 (windows in registers with borders exchanged by
+ * shuffles: widths of exactly 512 (radius <= 15) or 1024 (radius <= 16) -- the default
+ * where it applies); col_strip 0 (by shape), 16 (strips staged by the
  * tensor memory accelerator: heights up to 1024, width x sum bytes a multiple of 16),
  * 2, 4 or 8 (strips copied with cp.async, when the strip's column fits in shared
  * memory; 8 is the default up to height 1024). EINVAL for a choice that does not exist,

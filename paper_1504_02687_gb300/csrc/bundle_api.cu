@@ -1314,8 +1314,8 @@ static bundle_status tune_filter(bundle_ctx* c) {
     f.r = c->p.radius;
     f.passes = c->p.passes;
     bundle_status s;
-    for (int mode = 1; mode <= 2; ++mode) {
-        if (!rowbox_mode_valid(mode, c->W)) continue;
+    for (int mode = 1; mode <= 3; ++mode) {
+        if (!rowbox_mode_valid(mode, c->W, c->p.radius)) continue;
         f.row_mode = mode;
         for (int rep = 0; rep < 3; ++rep) {
             float ms = 0;
@@ -1458,7 +1458,7 @@ bundle_status bundle_set_tiles(bundle_ctx* c, int32_t eb, int32_t row_mode, int3
         return fail(&c->err, BUNDLE_ESTATE, "bundle_set_tiles: set the tiles of single contexts");
     if (eb != 0 && (eb < 4 || eb > kMaxEdgesPerWarp || (eb & (eb - 1)) != 0))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: eb must be 0, 4, 8, 16 or 32");
-    if (!rowbox_mode_valid(row_mode, c->W))
+    if (!rowbox_mode_valid(row_mode, c->W, c->p.radius))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: row variant %d does not exist for "
                     "width %d", row_mode, c->W);
     if (col_strip != 0 && !colbox_strip_valid(col_strip, c->W, c->H, c->p.radius, c->sum_bits / 8))

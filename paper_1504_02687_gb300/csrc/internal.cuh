@@ -109,7 +109,8 @@ struct FilterArgs {
     float inv_den_f;       // unused (kept for a future reciprocal form)
     float den_f;           // q (G - 1) s^k (or s^k for one group), rounded to float
     int32_t strip;         // column-pass strip: 16 (TMA-staged), 8, 4 or 2 (0: by shape)
-    int32_t row_mode;      // row pass: 0 by width, 1 register-resident rows, 2 shared-memory rows
+    int32_t row_mode;      // row pass: 0 by shape, 1 register-resident rows, 2 shared-memory
+                           // rows, 3 windows in registers with shuffled borders
     int32_t* err_flag;     // sticky device error word (2: a TMA copy did not land in time)
 };
 
@@ -184,7 +185,7 @@ cudaError_t launch_relayout_pairs(const float2* src, int32_t eb_src, int32_t cap
                                   int32_t eb_dst, int32_t cap_dst, int32_t* cnt_dst, int64_t E,
                                   cudaStream_t st);
 // Whether a row-pass / column-pass tile choice exists for this grid.
-bool rowbox_mode_valid(int mode, int W);
+bool rowbox_mode_valid(int mode, int W, int r);
 bool colbox_strip_valid(int strip, int W, int H, int r, int sum_bytes);
 // Sticky overflow flag: set when *mass > allowed.
 cudaError_t launch_check_mass(const unsigned long long* mass, unsigned long long allowed,

@@ -199,6 +199,122 @@ __global__ void __launch_bounds__(32 * kRowWarps)
     for (int x = lane; x < W; x += 32) Y[base + x] = buf[slot(x)];
 }
 
+// Row passes with the window in registers, for whole rows of 32 C cells and a radius R
+// known at compile time (R <= 16, R <= C). Lane l keeps E[0 .. C+2R]: cells
+// l*C - R - 1 .. l*C + C + R - 1 of the pass's input, its own chunk at E[R+1 .. R+C].
+// A pass fills the border -- the previous lane's last R+1 cells and the next lane's first
+// R, by shuffles; the row's two ends reflect the lane's own cells -- then runs the window
+// sum in registers, writing each output over the cell that just left the window, and
+// shifts the outputs back into place. Shared memory carries only the row's load and
+// store; the passes touch none, so a pass costs the L1 data pipe 2R+1 shuffles (two per
+// 64-bit value) instead of a shared load for every cell that enters or leaves a window.
+template <typename TS, int C, int R>
+__global__ void __launch_bounds__(32 * kRowWarps)
+    k_rowbox_shfl(const uint32_t* __restrict__ hist, int copies, TS* __restrict__ Y, int G,
+                  int H, int passes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int W = 32 * C;
+    constexpr int N = C + 2 * R + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    TS* buf = reinterpret_cast<TS*>(smem_raw) + (size_t)warp * (padded<C>(W) + 1);
+    const int g = blockIdx.y;
+    const int v = blockIdx.x * kRowWarps + warp;
+    if (v >= H) return;
+    const size_t base = ((size_t)g * H + v) * W;
+    const size_t stride_copy = (size_t)G * H * W;
+    // the row (copies summed) into shared memory, coalesced; then each lane's chunk
+    const uint4* h0 = reinterpret_cast<const uint4*>(hist + base);
+#pragma unroll
+    for (int it = 0; it < C / 4; ++it) {
+        const int x4 = lane + 32 * it;
+        uint4 u = __ldg(h0 + x4);
+        for (int k = 1; k < copies; ++k) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(hist + k * stride_copy + base) + x4);
+            u.x += w.x;
+            u.y += w.y;
+            u.z += w.z;
+            u.w += w.w;
+        }
+        const int x = 4 * x4;
+        buf[padded<C>(x)] = (TS)u.x;
+        buf[padded<C>(x + 1)] = (TS)u.y;
+        buf[padded<C>(x + 2)] = (TS)u.z;
+        buf[padded<C>(x + 3)] = (TS)u.w;
+    }
+    __syncwarp();
+    TS E[N];
+    const TS* mine = buf + padded<C>(lane * C);
+#pragma unroll
+    for (int q = 0; q < C; ++q) E[R + 1 + q] = mine[q];
+    for (int p = 0; p < passes; ++p) {
+        // border: cells -R-1 .. -1 of the chunk from the previous lane (lane 0: cells R .. 0
+        // of its own, the reflection), cells C .. C+R-1 from the next lane (lane 31: cells
+        // C-1 .. C-R of its own)
+#pragma unroll
+        for (int m = 0; m <= R; ++m) {
+            const TS left = __shfl_up_sync(0xffffffffu, E[C + m], 1);
+            E[m] = lane == 0 ? E[2 * R + 1 - m] : left;
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const TS right = __shfl_down_sync(0xffffffffu, E[R + 1 + m], 1);
+            E[R + 1 + C + m] = lane == 31 ? E[R + C - m] : right;
+        }
+        TS s = 0;
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) s += E[k];
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            s += E[q + 2 * R + 1] - E[q];
+            E[q] = s;  // output q over the cell that just left the window
+        }
+#pragma unroll
+        for (int q = C - 1; q >= 0; --q) E[R + 1 + q] = E[q];
+    }
+    __syncwarp();
+    TS* own = buf + padded<C>(lane * C);
+#pragma unroll
+    for (int q = 0; q < C; ++q) own[q] = E[R + 1 + q];
+    __syncwarp();
+    for (int x = lane; x < W; x += 32) Y[base + x] = buf[padded<C>(x)];
+}
+
+// The shuffle row pass exists for whole rows of 512 or 1024 cells and radii below the
+// lane's chunk, up to 16.
+inline bool rowbox_shfl_fits(int W, int r) {
+    return (W == 512 && r >= 1 && r <= 15) || (W == 1024 && r >= 1 && r <= 16);
+}
+
+template <typename TS, int C, int R>
+cudaError_t rowbox_shfl_launch(const FilterArgs& a, cudaStream_t st) {
+    const size_t smem = (size_t)kRowWarps * (padded<C>(32 * C) + 1) * sizeof(TS);
+    auto kern = k_rowbox_shfl<TS, C, R>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)((a.H + kRowWarps - 1) / kRowWarps), (unsigned)a.G);
+    kern<<<grid, 32 * kRowWarps, smem, st>>>(a.hist, a.hist_copies < 1 ? 1 : a.hist_copies,
+                                              static_cast<TS*>(a.Y), a.G, a.H, a.passes);
+    return cudaGetLastError();
+}
+
+// Dispatch on the radius: R runs from RMAX down to 1.
+template <typename TS, int C, int R>
+cudaError_t rowbox_shfl_r(const FilterArgs& a, cudaStream_t st) {
+    if constexpr (R < 1) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (a.r == R) return rowbox_shfl_launch<TS, C, R>(a, st);
+        return rowbox_shfl_r<TS, C, R - 1>(a, st);
+    }
+}
+
+template <typename TS>
+cudaError_t rowbox_shfl_t(const FilterArgs& a, cudaStream_t st) {
+    if (!rowbox_shfl_fits(a.W, a.r) || (a.W & 3)) return cudaErrorInvalidValue;
+    return a.W == 1024 ? rowbox_shfl_r<TS, 32, 16>(a, st) : rowbox_shfl_r<TS, 16, 15>(a, st);
+}
+
 // border width of the register row pass: r + 1 rounded up to a whole chunk
 inline int row_halo(int r, int C) { return (r + 1 + C - 1) / C * C; }
 
@@ -572,6 +688,9 @@ template <typename TS>
 cudaError_t rowbox_t(const FilterArgs& a, cudaStream_t st) {
     const int c = (a.W + 31) / 32;
     const int pad = (c % 2 == 0) ? 1 : 2;
+    // mode 3 (and the default where it fits): the window in registers, borders by shuffles
+    if (a.row_mode == 3 || (a.row_mode == 0 && rowbox_shfl_fits(a.W, a.r)))
+        return rowbox_shfl_t<TS>(a, st);
     if (a.row_mode != 2) {  // register-resident rows where a template exists for the width
         if (c == 32) return rowbox_reg_t<TS, 32>(a, st);
         if (c == 16) return rowbox_reg_t<TS, 16>(a, st);
@@ -677,9 +796,10 @@ cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-bool rowbox_mode_valid(int mode, int W) {
+bool rowbox_mode_valid(int mode, int W, int r) {
     const int c = (W + 31) / 32;
     if (mode == 1) return c == 8 || c == 16 || c == 32;
+    if (mode == 3) return rowbox_shfl_fits(W, r);
     return mode == 0 || mode == 2;
 }
 

@@ -617,3 +617,23 @@ def test_profile_counts_launches():
         assert all(ms >= 0 for ms, _ in prof.values())
     finally:
         pkg.bundle_destroy(ctx)
+
+
+@pytest.mark.parametrize("width,radius", [(512, 1), (512, 8), (512, 15), (1024, 4), (1024, 16)])
+def test_row_pass_variants_give_the_oracle_sums(width, radius):
+    """Every row-pass variant (register rows, shared-memory rows, windows in registers with
+    shuffled borders) gives the oracle's box sums (Sec. 3.1) bit for bit, at the widths and
+    radii the shuffled-border variant covers (its border spans up to a whole lane chunk)."""
+    w = synth.tiny(seed=60 + radius, n_edges=700, n_groups=2, grid=(width, 40), radius=radius,
+                   passes=3, n_fixed=0, n_max=32, weighted=True)
+    p = params_for(w)
+    for mode in (1, 2, 3):
+        ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+        try:
+            pkg.bundle_set_tiles(ctx, 0, mode, 0)
+            pkg.bundle_iterate(ctx, 2)
+            hist = pkg.bundle_fetch_density(ctx, pkg.DENSITY_HIST).astype(np.int64)
+            sums = pkg.bundle_fetch_density(ctx, pkg.DENSITY_SUMS).astype(np.int64)
+        finally:
+            pkg.bundle_destroy(ctx)
+        np.testing.assert_array_equal(sums, oracle.smooth(hist, radius, 3), err_msg=f"mode {mode}")
