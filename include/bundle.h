@@ -307,8 +307,12 @@ bundle_status bundle_autotune(bundle_ctx* ctx);
  * layout -- only on a fresh bundle_init context;
  * row_mode 0 (by shape), 1 (register rows, widths of 225..256, 481..512 or 993..1024
  * cells), 2 (shared-memory rows), 3 (windows in registers with borders exchanged by
- * shuffles: widths of exactly 512 (radius <= 15) or 1024 (radius <= 16) -- the default
- * where it applies); col_strip 0 (by shape), 16 (strips staged by the
+ * shuffles: widths of exactly 512 (radius <= 15) or 1024 (radius <= 16)), 4 (the banded
+ * path for both passes: the row passes stream bands of 8 rows through shared memory
+ * and write the result transposed, the column passes then run the same way over that
+ * -- widths and heights of exactly 512 (radius <= 15) or 1024 (radius <= 16); the
+ * default where it applies, 3 where only the width fits; col_strip is then unused);
+ * col_strip 0 (by shape), 16 (strips staged by the
  * tensor memory accelerator: heights up to 1024, width x sum bytes a multiple of 16),
  * 2, 4 or 8 (strips copied with cp.async, when the strip's column fits in shared
  * memory; 8 is the default up to height 1024). EINVAL for a choice that does not exist,

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbundle3dheb.so")
-SOURCES = ["bundle_api.cu", "k_points.cu", "k_grid.cu", "k_render.cu", "noalloc.cu"]
+SOURCES = ["bundle_api.cu", "k_points.cu", "k_grid.cu", "k_band.cu", "k_render.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-Xptxas", "-O3"]

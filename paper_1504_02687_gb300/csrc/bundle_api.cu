@@ -560,9 +560,10 @@ StepArgs make_step_args(bundle_ctx* c, int mode, int in, int out) {
     return a;
 }
 
-bundle_status run_step(bundle_ctx* c, int mode, int in, int out) {
+// hist_zero: the histogram is known to be zero already (the filter before cleared it).
+bundle_status run_step(bundle_ctx* c, int mode, int in, int out, bool hist_zero = false) {
     const StepArgs a = make_step_args(c, mode, in, out);
-    if (mode & kModeResample)
+    if ((mode & kModeResample) && !hist_zero)
         CUDA_TRY(&c->err, timed(c, kProfHistClear, [&] {
                      return cudaMemsetAsync(c->hist, 0,
                                             (size_t)kHistCopies * c->G * c->H * c->W * sizeof(uint32_t),
@@ -602,8 +603,12 @@ FilterArgs filter_args(bundle_ctx* c) {
     return f;
 }
 
-bundle_status run_filter(bundle_ctx* c) {
-    const FilterArgs f = filter_args(c);
+// clear: a splat follows, so the row pass may leave the histogram zero; *cleared (if
+// given) says whether it did.
+bundle_status run_filter(bundle_ctx* c, bool clear = false, bool* cleared = nullptr) {
+    FilterArgs f = filter_args(c);
+    f.clear_hist = clear ? 1 : 0;
+    if (cleared) *cleared = filter_clears_hist(f);
     if (c->ink)
         CUDA_TRY(&c->err, launch_ink(c->hist, (int64_t)c->H * c->W, c->G, kHistCopies, c->ink,
                                      c->d_iter, BUNDLE_INK_STATS_CAP, c->n_sm, c->stream));
@@ -653,9 +658,10 @@ bundle_status ensure_schedule(bundle_ctx* c, int32_t needed) {
 // One steady-state iteration: layer filter, mix into the density quads, histogram clear, the fused
 // advect -> resample -> splat step from buffer R to 1 - R, then the counter advance.
 bundle_status launch_iteration(bundle_ctx* c, int R) {
-    bundle_status s = run_filter(c);
+    bool cleared = false;
+    bundle_status s = run_filter(c, true, &cleared);
     if (s != BUNDLE_OK) return s;
-    s = run_step(c, kModeAdvectResample, R, 1 - R);
+    s = run_step(c, kModeAdvectResample, R, 1 - R, cleared);
     if (s != BUNDLE_OK) return s;
     CUDA_TRY(&c->err, launch_advance_iter(c->d_iter, c->stream));
     return BUNDLE_OK;
@@ -978,8 +984,9 @@ static bundle_status build_batch_graph(bundle_ctx* c, int R) {
         // every graph's filter on its own branch, then one step launch over all graphs
         for (size_t k = 0; k < c->members.size() && s == BUNDLE_OK; ++k) {
             bundle_ctx* m = c->members[k];
-            s = run_filter(m);
-            if (s == BUNDLE_OK &&
+            bool cleared = false;
+            s = run_filter(m, true, &cleared);
+            if (s == BUNDLE_OK && !cleared &&
                 cudaMemsetAsync(m->hist, 0, (size_t)kHistCopies * m->G * m->H * m->W * sizeof(uint32_t),
                                 m->stream) != cudaSuccess)
                 s = BUNDLE_ECUDA;
@@ -1298,7 +1305,8 @@ static bundle_status probe_prefix(bundle_ctx* c) {
 static bundle_status probe_step(bundle_ctx* c) { return run_step(c, kModeAdvectResample, 1, 0); }
 
 // Row-pass variant and column-pass strip of one context, timed on its current
-// histogram (best of three each).
+// histogram (best of three each), then the banded path (both passes) against the
+// fastest pair.
 static bundle_status tune_filter(bundle_ctx* c) {
     const int sb = c->sum_bits / 8;
     int best_row = c->row_mode, best_strip = c->col_strip;
@@ -1315,7 +1323,7 @@ static bundle_status tune_filter(bundle_ctx* c) {
     f.passes = c->p.passes;
     bundle_status s;
     for (int mode = 1; mode <= 3; ++mode) {
-        if (!rowbox_mode_valid(mode, c->W, c->p.radius)) continue;
+        if (!rowbox_mode_valid(mode, c->W, c->H, c->p.radius)) continue;
         f.row_mode = mode;
         for (int rep = 0; rep < 3; ++rep) {
             float ms = 0;
@@ -1341,6 +1349,25 @@ static bundle_status tune_filter(bundle_ctx* c) {
             if (ms < best_col_ms) {
                 best_col_ms = ms;
                 best_strip = strip;
+            }
+        }
+    }
+    // the banded path replaces both passes: timed as a pair against the best pair above
+    if (rowbox_mode_valid(4, c->W, c->H, c->p.radius)) {
+        f.row_mode = 4;
+        for (int rep = 0; rep < 3; ++rep) {
+            float ms = 0;
+            s = time_ms(c, [&] {
+                return launch_rowbox(c->sum_bits, f, c->stream) == cudaSuccess &&
+                               launch_colbox(c->sum_bits, f, c->stream) == cudaSuccess
+                           ? BUNDLE_OK
+                           : BUNDLE_ECUDA;
+            }, &ms);
+            if (s != BUNDLE_OK) return s;
+            if (ms < best_row_ms + best_col_ms) {
+                best_row_ms = ms;
+                best_col_ms = 0;
+                best_row = 4;
             }
         }
     }
@@ -1458,7 +1485,7 @@ bundle_status bundle_set_tiles(bundle_ctx* c, int32_t eb, int32_t row_mode, int3
         return fail(&c->err, BUNDLE_ESTATE, "bundle_set_tiles: set the tiles of single contexts");
     if (eb != 0 && (eb < 4 || eb > kMaxEdgesPerWarp || (eb & (eb - 1)) != 0))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: eb must be 0, 4, 8, 16 or 32");
-    if (!rowbox_mode_valid(row_mode, c->W, c->p.radius))
+    if (!rowbox_mode_valid(row_mode, c->W, c->H, c->p.radius))
         return fail(&c->err, BUNDLE_EINVAL, "bundle_set_tiles: row variant %d does not exist for "
                     "width %d", row_mode, c->W);
     if (col_strip != 0 && !colbox_strip_valid(col_strip, c->W, c->H, c->p.radius, c->sum_bits / 8))

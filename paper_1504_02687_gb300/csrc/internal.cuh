@@ -110,8 +110,11 @@ struct FilterArgs {
     float den_f;           // q (G - 1) s^k (or s^k for one group), rounded to float
     int32_t strip;         // column-pass strip: 16 (TMA-staged), 8, 4 or 2 (0: by shape)
     int32_t row_mode;      // row pass: 0 by shape, 1 register-resident rows, 2 shared-memory
-                           // rows, 3 windows in registers with shuffled borders
+                           // rows, 3 windows in registers with shuffled borders, 4 banded
+                           // rows for both passes (Y holds the transposed stack)
     int32_t* err_flag;     // sticky device error word (2: a TMA copy did not land in time)
+    int32_t clear_hist;    // 1: the row pass leaves the histogram zero where it can (the
+                           // banded path); filter_clears_hist tells whether it does
 };
 
 // Density quads. The gather side of the iteration reads each layer's density through
@@ -185,7 +188,19 @@ cudaError_t launch_relayout_pairs(const float2* src, int32_t eb_src, int32_t cap
                                   int32_t eb_dst, int32_t cap_dst, int32_t* cnt_dst, int64_t E,
                                   cudaStream_t st);
 // Whether a row-pass / column-pass tile choice exists for this grid.
-bool rowbox_mode_valid(int mode, int W, int r);
+bool rowbox_mode_valid(int mode, int W, int H, int r);
+// The k passes of the box filter along every row of a [G][NR][L] stack (L = 512 with
+// r <= 15, or 1024 with r <= 16), written transposed to [G][L][NR]. in: the histogram
+// (32-bit, `copies` copies copy_stride cells apart, summed) or, with sum_input, a sum
+// stack of the sum type; in 16-byte aligned, out 8-byte aligned. zero: null, or the
+// histogram itself (not with sum_input), whose rows are left zero once read.
+bool band_rows_fits(int L, int r);
+cudaError_t launch_band_rows(int sum_bits, bool sum_input, const void* in, int copies,
+                             int64_t copy_stride, void* out, int G, int NR, int L, int r,
+                             int passes, uint32_t* zero, cudaStream_t st);
+// Whether launch_rowbox with these arguments leaves the histogram zero (clear_hist set
+// and the banded path taken).
+bool filter_clears_hist(const FilterArgs& a);
 bool colbox_strip_valid(int strip, int W, int H, int r, int sum_bytes);
 // Sticky overflow flag: set when *mass > allowed.
 cudaError_t launch_check_mass(const unsigned long long* mass, unsigned long long allowed,

@@ -11,6 +11,7 @@
 // cancels exactly, so every box sum that fits its type is exact.
 #include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime)
 
+#include "box.cuh"
 #include "internal.cuh"
 
 namespace heb {
@@ -246,31 +247,7 @@ __global__ void __launch_bounds__(32 * kRowWarps)
     const TS* mine = buf + padded<C>(lane * C);
 #pragma unroll
     for (int q = 0; q < C; ++q) E[R + 1 + q] = mine[q];
-    for (int p = 0; p < passes; ++p) {
-        // border: cells -R-1 .. -1 of the chunk from the previous lane (lane 0: cells R .. 0
-        // of its own, the reflection), cells C .. C+R-1 from the next lane (lane 31: cells
-        // C-1 .. C-R of its own)
-#pragma unroll
-        for (int m = 0; m <= R; ++m) {
-            const TS left = __shfl_up_sync(0xffffffffu, E[C + m], 1);
-            E[m] = lane == 0 ? E[2 * R + 1 - m] : left;
-        }
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const TS right = __shfl_down_sync(0xffffffffu, E[R + 1 + m], 1);
-            E[R + 1 + C + m] = lane == 31 ? E[R + C - m] : right;
-        }
-        TS s = 0;
-#pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) s += E[k];
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            s += E[q + 2 * R + 1] - E[q];
-            E[q] = s;  // output q over the cell that just left the window
-        }
-#pragma unroll
-        for (int q = C - 1; q >= 0; --q) E[R + 1 + q] = E[q];
-    }
+    box_passes_shfl<TS, C, R>(E, lane, passes);
     __syncwarp();
     TS* own = buf + padded<C>(lane * C);
 #pragma unroll
@@ -796,11 +773,25 @@ cudaError_t colbox_t(const FilterArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-bool rowbox_mode_valid(int mode, int W, int r) {
+bool rowbox_mode_valid(int mode, int W, int H, int r) {
     const int c = (W + 31) / 32;
     if (mode == 1) return c == 8 || c == 16 || c == 32;
     if (mode == 3) return rowbox_shfl_fits(W, r);
+    if (mode == 4) return band_rows_fits(W, r) && band_rows_fits(H, r);
     return mode == 0 || mode == 2;
+}
+
+// Row mode 4, the banded path: both passes run the banded row kernel, the first writing
+// the row-filtered stack transposed ([G][W][H]) into Y, the second filtering Y's rows
+// (the columns) and writing them transposed back into S ([G][H][W]). Chosen by hand, by
+// the autotuner, or by shape when both sides fit and the buffers are aligned for it.
+static bool band_path(const FilterArgs& a) {
+    if (a.row_mode == 4) return true;
+    if (a.row_mode != 0 || !(band_rows_fits(a.W, a.r) && band_rows_fits(a.H, a.r))) return false;
+    const int copies = a.hist_copies < 1 ? 1 : a.hist_copies;
+    return copies <= 2 && (reinterpret_cast<uintptr_t>(a.hist) & 15) == 0 &&
+           (copies == 1 || ((int64_t)a.G * a.H * a.W * 4) % 16 == 0) &&
+           (reinterpret_cast<uintptr_t>(a.Y) & 15) == 0 && (reinterpret_cast<uintptr_t>(a.S) & 7) == 0;
 }
 
 bool colbox_strip_valid(int strip, int W, int H, int r, int sum_bytes) {
@@ -810,11 +801,20 @@ bool colbox_strip_valid(int strip, int W, int H, int r, int sum_bytes) {
            colbox_smem(H, r, strip, sum_bytes) <= (size_t)227 * 1024;
 }
 
+bool filter_clears_hist(const FilterArgs& a) { return a.clear_hist && band_path(a); }
+
 cudaError_t launch_rowbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
+    if (band_path(a))
+        return launch_band_rows(sum_bits, false, a.hist, a.hist_copies < 1 ? 1 : a.hist_copies,
+                                (int64_t)a.G * a.H * a.W, a.Y, a.G, a.H, a.W, a.r, a.passes,
+                                a.clear_hist ? const_cast<uint32_t*>(a.hist) : nullptr, st);
     return sum_bits == 32 ? rowbox_t<uint32_t>(a, st) : rowbox_t<unsigned long long>(a, st);
 }
 
 cudaError_t launch_colbox(int sum_bits, const FilterArgs& a, cudaStream_t st) {
+    if (band_path(a))
+        return launch_band_rows(sum_bits, true, a.Y, 1, 0, a.S, a.G, a.W, a.H, a.r, a.passes,
+                                nullptr, st);
     return sum_bits == 32 ? colbox_t<uint32_t>(a, st) : colbox_t<unsigned long long>(a, st);
 }
 

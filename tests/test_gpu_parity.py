@@ -637,3 +637,52 @@ def test_row_pass_variants_give_the_oracle_sums(width, radius):
         finally:
             pkg.bundle_destroy(ctx)
         np.testing.assert_array_equal(sums, oracle.smooth(hist, radius, 3), err_msg=f"mode {mode}")
+
+
+@pytest.mark.parametrize("sum_bits", [32, 64])
+@pytest.mark.parametrize("grid,radius", [((512, 512), 1), ((512, 512), 15), ((1024, 512), 7),
+                                         ((512, 1024), 12), ((1024, 1024), 16)])
+def test_banded_passes_give_the_oracle_sums(grid, radius, sum_bits):
+    """The banded path (row mode 4: the row passes over the histogram written transposed,
+    then the column passes as row passes over that, written back) gives the oracle's box
+    sums (Sec. 3.1) bit for bit, with 32- and 64-bit sums, on square and oblong grids and
+    at the radii its register windows cover; sums and densities equal the shared-memory
+    path's. 32-bit sums need a small mass (the library admits them only where the sum
+    bound fits)."""
+    small = sum_bits == 32
+    w = synth.tiny(seed=80 + radius, n_edges=20 if small else 1500, n_groups=3, grid=grid,
+                   radius=radius, passes=3, n_fixed=0, n_max=8 if small else 32,
+                   weighted=not small)
+    p = pkg.default_params(grid_w=grid[0], grid_h=grid[1], radius=radius, passes=3, n_fixed=0,
+                           n_max=8 if small else 32, sum_bits=sum_bits)
+    out = {}
+    for mode in (2, 4):
+        ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+        try:
+            pkg.bundle_set_tiles(ctx, 0, mode, 0)
+            pkg.bundle_iterate(ctx, 3)  # a middle iteration clears the histogram in its row pass
+            info = pkg.bundle_get_info(ctx)
+            assert info.tile_row == mode and info.sum_bits == sum_bits
+            out[mode] = (pkg.bundle_fetch_density(ctx, pkg.DENSITY_HIST).astype(np.int64),
+                         pkg.bundle_fetch_density(ctx, pkg.DENSITY_SUMS),
+                         pkg.bundle_fetch_density(ctx, pkg.DENSITY_RHO))
+        finally:
+            pkg.bundle_destroy(ctx)
+    hist, sums, rho = out[4]
+    assert hist.sum() > 0
+    np.testing.assert_array_equal(sums.astype(np.int64), oracle.smooth(hist, radius, 3))
+    np.testing.assert_array_equal(out[2][1], sums)
+    np.testing.assert_array_equal(out[2][2], rho)
+
+
+def test_banded_path_rejected_where_it_does_not_fit():
+    """Row mode 4 needs both sides of 512 or 1024 cells and a radius its windows cover."""
+    w = synth.tiny(seed=5, n_edges=200, n_groups=2, grid=(512, 40), radius=4, passes=2,
+                   n_fixed=0, n_max=16, weighted=False)
+    ctx = pkg.bundle_init(params_for(w), w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+    try:
+        with pytest.raises(pkg.BundleError) as ei:
+            pkg.bundle_set_tiles(ctx, 0, 4, 0)
+        assert ei.value.status == pkg.BUNDLE_EINVAL
+    finally:
+        pkg.bundle_destroy(ctx)
