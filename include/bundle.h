@@ -89,6 +89,12 @@ typedef struct {
                                    (occupied histogram cells): the convergence measure of
                                    bundle_fetch_ink (Sec. 3.3, Fig. 3 compares convergence of
                                    the two steps; fewer occupied cells = tighter bundles) */
+#define BUNDLE_FLAG_LOAD_GATHERS 8 /* the advection's density gathers read the quad map through
+                                      the load path; default: through a texture view of the same
+                                      map (point sampled, the same bits), where the map's quads
+                                      fit a 1D texture (the device's 1D linear texture width
+                                      limit, in quads). Results are identical;
+                                      only the speed differs. */
 
 /* Result of bundle_get_info. */
 typedef struct {

@@ -27,6 +27,7 @@ INPUT_DEVICE = 1
 FLAG_FIXED_STEP = 1
 FLAG_SEGMENT_HIST = 2
 FLAG_INK_STATS = 4
+FLAG_LOAD_GATHERS = 8
 INK_STATS_CAP = 4096
 FETCH_DEVICE, FETCH_PIXELS, FETCH_RESAMPLED = 1, 2, 4
 STEP_LAST = 1

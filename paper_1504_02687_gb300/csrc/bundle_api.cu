@@ -54,6 +54,7 @@ struct bundle_ctx {
     void* S = nullptr;
     void* rho = nullptr;
     void* quads = nullptr;   // [G][H+3][W+3] density quads
+    cudaTextureObject_t qtex = 0;  // texture view of the quads (0 where it cannot be made)
     unsigned long long* counters = nullptr;  // [0] points splatted, [1] scratch sum, [2] segment mass
     int64_t* fetch_off = nullptr;
     int64_t* fetch_tmp = nullptr;
@@ -152,6 +153,7 @@ void free_ctx(bundle_ctx* c) {
     }
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->qtex) cudaDestroyTextureObject(c->qtex);
     void* ptrs[] = {c->perm, c->group, c->weight, c->cnt[0], c->cnt[1], c->pts[0], c->pts[1],
                     c->hist, c->Y, c->S, c->rho, c->quads, c->mix, c->d_flag, c->ink, c->counters, c->fetch_off, c->fetch_tmp,
                     c->fetch_xy};
@@ -209,7 +211,7 @@ bundle_status check_params(const bundle_params& p, int32_t n_groups, std::string
     if (p.grid_dominant < 2 || p.grid_dominant > 4096)
         return fail(e, BUNDLE_EINVAL, "grid_dominant must be in [2, 4096]");
     if ((p.flags & ~(BUNDLE_FLAG_FIXED_STEP | BUNDLE_FLAG_SEGMENT_HIST |
-                     BUNDLE_FLAG_INK_STATS)) != 0)
+                     BUNDLE_FLAG_INK_STATS | BUNDLE_FLAG_LOAD_GATHERS)) != 0)
         return fail(e, BUNDLE_EINVAL, "unknown bits in flags");
     if (!(p.directed_offset >= 0 && p.directed_offset < 0.25f))
         return fail(e, BUNDLE_EINVAL, "directed_offset must be in [0, 0.25)");
@@ -362,6 +364,30 @@ bundle_status grid_map(bundle_ctx* c, const float* src, const float* dst, std::s
 }
 
 // Device buffers sized from E, cap, G, H, W and the widths.
+// The quad map's density gathers go through the texture path: a 1D texture over the
+// linear quad map (one texel per quad, point sampled: the stored values bit for bit) moves
+// them off the load/store data pipe, which the step kernel's shared-memory work and point
+// traffic keep busy. Maps with more quads than a 1D texture holds keep the load path.
+cudaError_t make_quad_texture(bundle_ctx* c) {
+    const size_t n = (size_t)c->G * quad_elems(c->W, c->H);
+    int max_w = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture1DLinearWidth, c->device);
+    if (e != cudaSuccess) return e;
+    if (n > (size_t)max_w || n > (size_t)INT32_MAX || (c->p.flags & BUNDLE_FLAG_LOAD_GATHERS))
+        return cudaSuccess;  // load path
+    cudaResourceDesc rd{};
+    rd.resType = cudaResourceTypeLinear;
+    rd.res.linear.devPtr = c->quads;
+    rd.res.linear.desc = c->p.rho_dtype == BUNDLE_RHO_F32 ? cudaCreateChannelDesc<float4>()
+                                                          : cudaCreateChannelDesc<ushort4>();
+    rd.res.linear.sizeInBytes = n * 4 * rho_bytes(c->p.rho_dtype);
+    cudaTextureDesc td{};
+    td.readMode = cudaReadModeElementType;
+    td.filterMode = cudaFilterModePoint;
+    td.addressMode[0] = cudaAddressModeClamp;
+    return cudaCreateTextureObject(&c->qtex, &rd, &td, nullptr);
+}
+
 bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     const int64_t E = c->E;
     // blocks of up to 32 edges, one warp each; small graphs use smaller blocks so that at
@@ -388,6 +414,7 @@ bundle_status alloc_state(bundle_ctx* c, std::string* e) {
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->rho), C * rho_bytes(c->p.rho_dtype)));
     CUDA_TRY(e, dalloc(c, reinterpret_cast<unsigned char**>(&c->quads),
                        (size_t)c->G * quad_elems(c->W, c->H) * 4 * rho_bytes(c->p.rho_dtype)));
+    CUDA_TRY(e, make_quad_texture(c));
     CUDA_TRY(e, dalloc(c, &c->counters, 4));
     CUDA_TRY(e, dalloc(c, &c->d_iter, 1));
     CUDA_TRY(e, dalloc(c, &c->d_flag, 1));
@@ -532,6 +559,7 @@ StepArgs make_step_args(bundle_ctx* c, int mode, int in, int out) {
     a.group = c->group;
     a.weight = c->weight;
     a.quads = c->quads;
+    a.qtex = c->qtex;
     a.hist = c->hist;
     a.n_splat = c->counters;
     a.E = c->E;

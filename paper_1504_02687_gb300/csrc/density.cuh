@@ -31,6 +31,42 @@ __device__ __forceinline__ float4 load_quad<__half>(const __half* Q, int64_t i) 
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The same quads through the texture path: texel i of the 1D view is quad i (16-bit
+// densities come back as their bit patterns).
+template <typename T>
+__device__ __forceinline__ float4 fetch_quad(unsigned long long tex, int64_t i);
+template <>
+__device__ __forceinline__ float4 fetch_quad<float>(unsigned long long tex, int64_t i) {
+    return tex1Dfetch<float4>((cudaTextureObject_t)tex, (int)i);
+}
+template <>
+__device__ __forceinline__ float4 fetch_quad<__nv_bfloat16>(unsigned long long tex, int64_t i) {
+    const ushort4 u = tex1Dfetch<ushort4>((cudaTextureObject_t)tex, (int)i);
+    return make_float4(__bfloat162float(__ushort_as_bfloat16(u.x)),
+                       __bfloat162float(__ushort_as_bfloat16(u.y)),
+                       __bfloat162float(__ushort_as_bfloat16(u.z)),
+                       __bfloat162float(__ushort_as_bfloat16(u.w)));
+}
+template <>
+__device__ __forceinline__ float4 fetch_quad<__half>(unsigned long long tex, int64_t i) {
+    const ushort4 u = tex1Dfetch<ushort4>((cudaTextureObject_t)tex, (int)i);
+    return make_float4(__half2float(__ushort_as_half(u.x)), __half2float(__ushort_as_half(u.y)),
+                       __half2float(__ushort_as_half(u.z)), __half2float(__ushort_as_half(u.w)));
+}
+
+// One layer of the quad map as the gathers see it: through the texture view of the whole
+// map (TEX) or through the load path (the kernel is compiled for one of the two).
+template <typename T, bool TEX>
+struct QuadMap {
+    const T* q;              // the layer's quads
+    unsigned long long tex;  // texture view of the whole map
+    int64_t base;            // the layer's first quad in the texture view
+    __device__ __forceinline__ float4 at(int64_t i) const {
+        if constexpr (TEX) return fetch_quad<T>(tex, base + i);
+        else return load_quad(q, i);
+    }
+};
+
 __device__ __forceinline__ float lerp_rn(float a, float b, float f) {
     return __fmaf_rn(f, __fsub_rn(b, a), a);
 }
@@ -63,6 +99,12 @@ __device__ __forceinline__ float density_at(const T* __restrict__ Q, int W, int 
                                             float y) {
     Frame f = frame_of(x, y, W, H);
     return bilinear(load_quad(Q, (int64_t)(f.b0 + 2) * (W + kQuadPad) + (f.a0 + 2)), f.fu, f.fv);
+}
+template <typename T, bool TEX>
+__device__ __forceinline__ float density_at(const QuadMap<T, TEX>& m, int W, int H, float x,
+                                            float y) {
+    Frame f = frame_of(x, y, W, H);
+    return bilinear(m.at((int64_t)(f.b0 + 2) * (W + kQuadPad) + (f.a0 + 2)), f.fu, f.fv);
 }
 
 __device__ __forceinline__ float clamp_pos(float v, int n) {

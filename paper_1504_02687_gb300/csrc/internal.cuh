@@ -38,6 +38,7 @@ enum StepMode : int {
     kModeResample = 2,                // resample + splat the input polylines
     kModeAdvect = 1,                  // advect + Laplacian, write polylines
     kModeAdvectResample = 3,          // advect + Laplacian + resample + splat
+    kModeTexGather = 4,               // (with kModeAdvect) density gathers via StepArgs::qtex
 };
 
 struct StepArgs {
@@ -48,6 +49,8 @@ struct StepArgs {
     const int32_t* group;    // [E] per slot
     const int32_t* weight;   // [E] per slot
     const void* quads;       // [G][H+3][W+3] density quads (see below), rho type x 4
+    unsigned long long qtex; // the same quads as a 1D texture (texel i = quad i), or 0: the
+                             // gathers then read `quads` through the load path
     uint32_t* hist;          // [G][H][W] histogram accumulated by the splat
     unsigned long long* n_splat;  // running count of splatted points
     int64_t E;

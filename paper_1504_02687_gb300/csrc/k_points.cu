@@ -18,15 +18,15 @@ struct Dir {
     float dx, dy, rho0;
 };
 
-template <typename T>
-__device__ __forceinline__ Dir direction(float2 p, const T* __restrict__ Q, int W, int H,
+template <typename T, bool TEX>
+__device__ __forceinline__ Dir direction(float2 p, const QuadMap<T, TEX>& Q, int W, int H,
                                          float eps) {
     Frame f = frame_of(p.x, p.y, W, H);
     const int64_t Wq = W + kQuadPad;
     const int64_t c = (int64_t)(f.b0 + 2) * Wq + (f.a0 + 2);
     // quads at (a0, b0-1), (a0-1, b0), (a0+1, b0), (a0, b0+1): the 12-cell stencil
-    const float4 up = load_quad(Q, c - Wq), lf = load_quad(Q, c - 1);
-    const float4 rt = load_quad(Q, c + 1), dn = load_quad(Q, c + Wq);
+    const float4 up = Q.at(c - Wq), lf = Q.at(c - 1);
+    const float4 rt = Q.at(c + 1), dn = Q.at(c + Wq);
     // E(a0,b0) = up.z, E(a0+1,b0) = up.w, E(a0,b0+1) = dn.x, E(a0+1,b0+1) = dn.y
     // central differences (E(a+1) - E(a-1)) / 2 at the four cell centres, interpolated;
     // halving commutes exactly with the interpolation (a power-of-two scaling), so it is
@@ -139,7 +139,7 @@ struct StepSmem {
 // Advection of the staged interior points (Eq. 5, Sec. 3.3), one thread per point:
 // the direction, then step trials of size h, h/2, ... until the density at the
 // moved position is not lower than at the point (none accepted: the point stays).
-template <typename T>
+template <typename T, bool TEX>
 __device__ __forceinline__ void advect_staged(const StepArgs& a, StepSmem& S, int np, int p0,
                                               const T* quads, int64_t QC4, float h) {
     const int lane = threadIdx.x & 31;
@@ -149,7 +149,7 @@ __device__ __forceinline__ void advect_staged(const StepArgs& a, StepSmem& S, in
         const int q = md.x - p0, n = md.y, g = md.z;
         const int j = k - q;
         if (k < np && j > 0 && j < n - 1) {
-            const T* Q = quads + (int64_t)g * QC4;
+            const QuadMap<T, TEX> Q{quads + (int64_t)g * QC4, a.qtex, (int64_t)g * (QC4 / 4)};
             const float2 p = S.pts[k];
             const Dir d = direction(p, Q, a.W, a.H, a.eps);
             if (a.fixed_step) {  // KDEEB's step (Sec. 3.3): h whatever the density there
@@ -228,7 +228,8 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, int64_t blk, StepSm
         }
         __syncwarp();
 
-        if (MODE & kModeAdvect) advect_staged<T>(a, S, np, p0, quads, QC4, h);
+        if (MODE & kModeAdvect)
+            advect_staged<T, (MODE & kModeTexGather) != 0>(a, S, np, p0, quads, QC4, h);
 
         // one polyline at a time, two consecutive points per lane (j = 2 lane, 2 lane + 1;
         // a polyline has at most 64 points): Laplacian smoothing, then the arc lengths. The
@@ -380,8 +381,14 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, int64_t blk, StepSm
         atomicAdd(a.n_splat, (unsigned long long)out_base);
 }
 
+// CTAs per SM the step kernels are compiled for, a register budget of 65536 / (128 x n):
+// 10 (48 registers) where the gathers take the texture path, 9 (56) elsewhere -- the
+// load-path and resample-only forms spill at 48 (measured fastest of 8 to 11).
+template <int MODE>
+constexpr int step_min_ctas() { return (MODE & kModeTexGather) ? 10 : 9; }
+
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kStepThreads, 8) k_step(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(kStepThreads, step_min_ctas<MODE>()) k_step(const __grid_constant__ StepArgs a) {
     __shared__ StepSmem smem[kStepWarps];
     const int warp = threadIdx.x >> 5;
     step_warp<MODE, T>(a, (int64_t)blockIdx.x * kStepWarps + warp, smem[warp]);
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_step(const __grid_constant_
 // Many graphs in one launch: CTA blockIdx.x belongs to graph m with
 // blk[m] <= blockIdx.x < blk[m + 1] and is that graph's CTA blockIdx.x - blk[m].
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kStepThreads, 8) k_step_batch(const __grid_constant__ BatchStepArgs P) {
+__global__ void __launch_bounds__(kStepThreads, step_min_ctas<MODE>()) k_step_batch(const __grid_constant__ BatchStepArgs P) {
     __shared__ StepSmem smem[kStepWarps];
     int lo = 0, hi = P.n - 1;
     while (lo < hi) {
@@ -413,11 +420,20 @@ cudaError_t launch_step_batch_t(int mode, const BatchStepArgs& P, cudaStream_t s
     if (total <= 0) return cudaSuccess;
     for (int m = 0; m < P.n; ++m)
         if (P.a[m].eb < 1 || P.a[m].eb > kMaxEdgesPerWarp) return cudaErrorInvalidValue;
-    switch (mode) {
+    // gathers through the texture views when every graph has one
+    bool tex = true;
+    for (int m = 0; m < P.n; ++m) tex = tex && P.a[m].qtex != 0;
+    switch (mode | ((mode & kModeAdvect) && tex ? kModeTexGather : 0)) {
         case kModeResample: k_step_batch<kModeResample, T><<<total, kStepThreads, 0, st>>>(P); break;
         case kModeAdvect: k_step_batch<kModeAdvect, T><<<total, kStepThreads, 0, st>>>(P); break;
         case kModeAdvectResample:
             k_step_batch<kModeAdvectResample, T><<<total, kStepThreads, 0, st>>>(P);
+            break;
+        case kModeAdvect | kModeTexGather:
+            k_step_batch<kModeAdvect | kModeTexGather, T><<<total, kStepThreads, 0, st>>>(P);
+            break;
+        case kModeAdvectResample | kModeTexGather:
+            k_step_batch<kModeAdvectResample | kModeTexGather, T><<<total, kStepThreads, 0, st>>>(P);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -429,11 +445,17 @@ cudaError_t launch_step_t(int mode, const StepArgs& a, cudaStream_t st) {
     if (a.E <= 0) return cudaSuccess;
     if (a.eb < 1 || a.eb > kMaxEdgesPerWarp) return cudaErrorInvalidValue;
     dim3 grid((unsigned)step_ctas(a.E, a.eb));
-    switch (mode) {
+    switch (mode | ((mode & kModeAdvect) && a.qtex ? kModeTexGather : 0)) {
         case kModeResample: k_step<kModeResample, T><<<grid, kStepThreads, 0, st>>>(a); break;
         case kModeAdvect: k_step<kModeAdvect, T><<<grid, kStepThreads, 0, st>>>(a); break;
         case kModeAdvectResample:
             k_step<kModeAdvectResample, T><<<grid, kStepThreads, 0, st>>>(a);
+            break;
+        case kModeAdvect | kModeTexGather:
+            k_step<kModeAdvect | kModeTexGather, T><<<grid, kStepThreads, 0, st>>>(a);
+            break;
+        case kModeAdvectResample | kModeTexGather:
+            k_step<kModeAdvectResample | kModeTexGather, T><<<grid, kStepThreads, 0, st>>>(a);
             break;
         default: return cudaErrorInvalidValue;
     }

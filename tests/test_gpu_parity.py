@@ -686,3 +686,35 @@ def test_banded_path_rejected_where_it_does_not_fit():
         assert ei.value.status == pkg.BUNDLE_EINVAL
     finally:
         pkg.bundle_destroy(ctx)
+
+
+@pytest.mark.parametrize("rho_dtype", [pkg.RHO_F32, pkg.RHO_BF16, pkg.RHO_F16])
+def test_texture_gathers_equal_load_gathers(rho_dtype):
+    """The advection's density gathers through the texture view of the quad map (the default)
+    and through the load path (FLAG_LOAD_GATHERS) give the same polylines, histograms and
+    densities bit for bit, for every density storage type, in single runs and in a batch."""
+    w = synth.tiny(**WORKLOADS["g3-bylength-weighted"])
+    w2 = synth.tiny(**WORKLOADS["g5-bylength-r2k4"])
+    res = []
+    for flags in (0, pkg.FLAG_LOAD_GATHERS):
+        p = params_for(w, rho_dtype=rho_dtype, flags=flags)
+        ctx = pkg.bundle_init(p, w.src_xy, w.dst_xy, w.group, w.n_groups, w.weight)
+        try:
+            pkg.bundle_iterate(ctx, 4)
+            off, xy = pkg.bundle_fetch(ctx, pixels=True)
+            res.append([off, xy, pkg.bundle_fetch_density(ctx, pkg.DENSITY_HIST),
+                        pkg.bundle_fetch_density(ctx, pkg.DENSITY_RHO)])
+        finally:
+            pkg.bundle_destroy(ctx)
+        ps = [params_for(v, rho_dtype=rho_dtype, flags=flags) for v in (w, w2)]
+        descs = [dict(src_xy=v.src_xy, dst_xy=v.dst_xy, group=v.group, n_groups=v.n_groups,
+                      weight=v.weight) for v in (w, w2)]
+        b = pkg.bundle_init_batch(descs, ps)
+        try:
+            pkg.bundle_iterate(b, 4)
+            for k in range(2):
+                res[-1].extend(pkg.bundle_fetch(pkg.bundle_batch_member(b, k), pixels=True))
+        finally:
+            pkg.bundle_destroy(b)
+    for x, y in zip(res[0], res[1]):
+        np.testing.assert_array_equal(x, y)

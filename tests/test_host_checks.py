@@ -37,7 +37,7 @@ def _edges(E, seed=0):
     (dict(grid_w=8192, grid_h=64), "grid"),
     (dict(grid_w=16, grid_h=16, radius=16, margin_px=0), "radius"),
     (dict(grid_w=16, grid_h=16, radius=4, margin_px=8), "margin"),
-    (dict(flags=8), "flags"),
+    (dict(flags=16), "flags"),
     (dict(flags=2, sum_bits=32), "64-bit sums"),
     (dict(directed_offset=0.5), "directed_offset"),
 ])
