@@ -237,6 +237,20 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, int64_t blk, StepSm
         for (int i = b0; i < b1; ++i) {
             const int4 md = S.meta[i];
             const int q = md.x - p0, n = md.y;
+            if (n == 2) {
+                // end points only (a quarter of a bundled layout's edges are this short):
+                // nothing to smooth, one segment; the same values as the general path
+                if (MODE & kModeResample) {
+                    if (lane == 0) {
+                        S.cum[q] = 0.0f;
+                        S.cum[q + 1] = seg_len(S.pts[q], S.pts[q + 1]);
+                    }
+                } else {
+                    if (lane < 2) pout[p0 + q + lane] = S.pts[q + lane];
+                    if (lane == 0) a.cnt_out[e0 + i] = n;
+                }
+                continue;
+            }
             const int j0 = 2 * lane, j1 = j0 + 1;
             float2 A0 = j0 < n ? S.pts[q + j0] : make_float2(0.0f, 0.0f);
             float2 A1 = j1 < n ? S.pts[q + j1] : make_float2(0.0f, 0.0f);
@@ -305,6 +319,14 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, int64_t blk, StepSm
                 const int4 md = S.meta[i], mo = S.outm[i];
                 const int q = md.x - p0, n = md.y, g = md.z, w = md.w;
                 const int m = mo.x, ob = mo.y;
+                if (m == 2 && !a.seg_hist) {
+                    // the two end points, copied and splatted (one lane each)
+                    if (lane < 2)
+                        emit(a, hist + (size_t)g * a.W * a.H, pout + ob + lane,
+                             S.pts[q + (lane == 0 ? 0 : n - 1)], w);
+                    if (lane == 0) a.cnt_out[e0 + i] = m;
+                    continue;
+                }
                 const float spi = __int_as_float(mo.z);
                 const float L = S.cum[q + n - 1];
                 uint32_t* hl = hist + (size_t)g * a.W * a.H;
