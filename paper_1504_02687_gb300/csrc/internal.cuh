@@ -20,7 +20,7 @@ constexpr int kEdgesPerBlock = 128;
 constexpr int kMaxEdgesPerWarp = 32;  // one slot per lane
 constexpr int kStepWarps = 4;         // warps per CTA of the step kernel, one block each
 constexpr int kStepThreads = 32 * kStepWarps;
-constexpr int kStage = 128;           // points of whole polylines staged per warp
+constexpr int kStage = 192;           // points of whole polylines staged per warp
 constexpr int kMaxCap = 64;           // largest polyline (n_fixed or n_max): two points per lane
 constexpr float kEdgeGuard = 0.0009765625f;  // positions stay below W - 2^-10
 // CTAs of one step launch over E edges in blocks of eb.
