@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
     using Lay = BandLayout<TIn, C>;
     constexpr int L = Lay::L, P = Lay::P, RS = Lay::RS;
     constexpr int NS = kBandStages;
-    constexpr int XS = kBandThreads / kBandRows;  // columns a store round covers
+    constexpr int XS = kBandThreads / kBandRows;  // columns one sweep of the stores covers
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per_layer = (NR + kBandRows - 1) / kBandRows;
