@@ -367,12 +367,15 @@ bundle_status grid_map(bundle_ctx* c, const float* src, const float* dst, std::s
 // The quad map's density gathers go through the texture path: a 1D texture over the
 // linear quad map (one texel per quad, point sampled: the stored values bit for bit) moves
 // them off the load/store data pipe, which the step kernel's shared-memory work and point
-// traffic keep busy. Maps with more quads than a 1D texture holds keep the load path.
+// traffic keep busy. Maps with more quads than a 1D texture holds keep the load path, and so
+// does a context whose texture cannot be made (the view is a speed-up, not a requirement).
 cudaError_t make_quad_texture(bundle_ctx* c) {
     const size_t n = (size_t)c->G * quad_elems(c->W, c->H);
     int max_w = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture1DLinearWidth, c->device);
-    if (e != cudaSuccess) return e;
+    if (cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture1DLinearWidth, c->device) != cudaSuccess) {
+        (void)cudaGetLastError();  // the launches after it check the last error
+        return cudaSuccess;        // load path
+    }
     if (n > (size_t)max_w || n > (size_t)INT32_MAX || (c->p.flags & BUNDLE_FLAG_LOAD_GATHERS))
         return cudaSuccess;  // load path
     cudaResourceDesc rd{};
@@ -385,7 +388,11 @@ cudaError_t make_quad_texture(bundle_ctx* c) {
     td.readMode = cudaReadModeElementType;
     td.filterMode = cudaFilterModePoint;
     td.addressMode[0] = cudaAddressModeClamp;
-    return cudaCreateTextureObject(&c->qtex, &rd, &td, nullptr);
+    if (cudaCreateTextureObject(&c->qtex, &rd, &td, nullptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->qtex = 0;
+    }
+    return cudaSuccess;
 }
 
 bundle_status alloc_state(bundle_ctx* c, std::string* e) {
