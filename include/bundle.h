@@ -301,7 +301,8 @@ bundle_status bundle_render(bundle_ctx* ctx, const bundle_render_params* params,
  * its own edges), times on the GPU: the edges per block of the point kernels (4, 8,
  * 16, 32 -- one warp works through each block; each candidate resamples, splats and filters the straight edges, then
  * the fused advect + resample step is timed), the row-pass variant and the column-pass
- * strip, and keeps the fastest of each (bundle_info.tile_*). Results do not depend on
+ * strip, then the banded path (row mode 4, both passes) against the fastest pair, and
+ * keeps the fastest of each (bundle_info.tile_*). Results do not depend on
  * the tiles: every choice gives the same bits. The context returns to its fresh state
  * (iteration 0). ESTATE after an iteration, for bundle_init_polylines contexts and for
  * batch members; synchronises the stream; allocates E * 32 bytes while it runs.
