@@ -93,8 +93,8 @@ typedef struct {
                                       the load path; default: through a texture view of the same
                                       map (point sampled, the same bits), where the map's quads
                                       fit a 1D texture (the device's 1D linear texture width
-                                      limit, in quads). Results are identical;
-                                      only the speed differs. */
+                                      limit, in quads) and the texture can be made. Results
+                                      are identical; only the speed differs. */
 
 /* Result of bundle_get_info. */
 typedef struct {
@@ -112,7 +112,8 @@ typedef struct {
                                    over iterations of the points each iteration advects */
     int32_t tile_eb;            /* edges per block of the point kernels */
     int32_t tile_row;           /* row-pass variant: 0 by shape, 1 register rows, 2 shared rows,
-                                   3 register windows with shuffled borders */
+                                   3 register windows with shuffled borders, 4 banded passes
+                                   for both axes */
     int32_t tile_strip;         /* column-pass strip: 0 by shape, else 16 (TMA), 8, 4 or 2 */
     int32_t reserved;
 } bundle_info;
