@@ -99,3 +99,40 @@ def test_init_without_gpu_fails_cleanly(built):
     with pytest.raises(pkg.BundleError) as ei:
         pkg.bundle_init(pkg.default_params(grid_w=64, grid_h=64), src, dst)
     assert ei.value.status in (pkg.BUNDLE_ECUDA, pkg.BUNDLE_ENOMEM)
+
+
+def test_binding_constants_match_the_header():
+    """Every #define and status value the binding mirrors has the header's value."""
+    import paper_1504_02687_gb300 as pkg
+
+    txt = open(HEADER).read()
+    defs = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"^#define (BUNDLE_[A-Z_0-9]+) (\d+)", txt, flags=re.M)}
+    pairs = {"BUNDLE_FLAG_FIXED_STEP": pkg.FLAG_FIXED_STEP,
+             "BUNDLE_FLAG_SEGMENT_HIST": pkg.FLAG_SEGMENT_HIST,
+             "BUNDLE_FLAG_INK_STATS": pkg.FLAG_INK_STATS,
+             "BUNDLE_FLAG_LOAD_GATHERS": pkg.FLAG_LOAD_GATHERS,
+             "BUNDLE_INPUT_DEVICE": pkg.INPUT_DEVICE,
+             "BUNDLE_FETCH_DEVICE": pkg.FETCH_DEVICE,
+             "BUNDLE_FETCH_PIXELS": pkg.FETCH_PIXELS,
+             "BUNDLE_FETCH_RESAMPLED": pkg.FETCH_RESAMPLED,
+             "BUNDLE_DENSITY_HIST": pkg.DENSITY_HIST,
+             "BUNDLE_DENSITY_SUMS": pkg.DENSITY_SUMS,
+             "BUNDLE_DENSITY_RHO": pkg.DENSITY_RHO,
+             "BUNDLE_INK_STATS_CAP": pkg.INK_STATS_CAP,
+             "BUNDLE_PROFILE_KINDS": len(pkg.PROFILE_KINDS),
+             "BUNDLE_STEP_LAST": pkg.STEP_LAST}
+    for name, value in pairs.items():
+        assert defs[name] == value, name
+    # the flags are distinct bits
+    flags = [v for k, v in defs.items() if k.startswith("BUNDLE_FLAG_")]
+    assert len(flags) == len(set(flags)) and all(f & (f - 1) == 0 for f in flags)
+    # status and density-type enums
+    for name in ("BUNDLE_OK", "BUNDLE_EINVAL", "BUNDLE_ENOMEM", "BUNDLE_ECUDA", "BUNDLE_EOVERFLOW",
+                 "BUNDLE_ETIMEOUT", "BUNDLE_ESTATE", "BUNDLE_ENOTSUP"):
+        m = re.search(rf"\b{name} = (\d+)", txt)
+        assert m and int(m.group(1)) == getattr(pkg, name), name
+    for name, attr in (("BUNDLE_RHO_F32", "RHO_F32"), ("BUNDLE_RHO_BF16", "RHO_BF16"),
+                       ("BUNDLE_RHO_F16", "RHO_F16")):
+        m = re.search(rf"\b{name} = (\d+)", txt)
+        assert m and int(m.group(1)) == getattr(pkg, attr), name
